@@ -1,0 +1,365 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+rational solutions, brute-force sums, the matrix exponential of the Maxwell
+ODE, closed-form plane waves, invariants and an exact special case of the
+decomposition.  CPU only.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import psatd_oracle as O
+from paper_1707_08500_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# order-p weights (Sec. 3.1 substitution)
+# --------------------------------------------------------------------------
+def _solve_exact(rows, rhs):
+    """Gauss-Jordan elimination over the rationals."""
+    n = len(rhs)
+    a = [list(r) + [b] for r, b in zip(rows, rhs)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if a[r][c] != 0)
+        a[c], a[piv] = a[piv], a[c]
+        for r in range(n):
+            if r != c and a[r][c] != 0:
+                f = a[r][c] / a[c][c]
+                a[r] = [x - f * y for x, y in zip(a[r], a[c])]
+    return [a[i][n] / a[i][i] for i in range(n)]
+
+
+def exact_weights(p, staggered):
+    """Weights from the Taylor moment conditions: the stencil differentiates
+    x exactly and annihilates x^3, x^5, ..., x^(p-1)."""
+    m = p // 2
+    off = [Fraction(2 * j - 1, 2) if staggered else Fraction(j) for j in range(1, m + 1)]
+    rows = [[2 * o ** l for o in off] for l in range(1, 2 * m, 2)]
+    rhs = [Fraction(1)] + [Fraction(0)] * (m - 1)
+    return _solve_exact(rows, rhs)
+
+
+@pytest.mark.parametrize("p", list(range(2, 22, 2)))
+@pytest.mark.parametrize("staggered", [False, True])
+def test_fd_weights_match_exact_moment_solution(p, staggered):
+    ex = [float(v) for v in exact_weights(p, staggered)]
+    got = O.fd_weights_staggered(p) if staggered else O.fd_weights_nodal(p)
+    np.testing.assert_allclose(got, ex, rtol=1e-13, atol=0)
+
+
+def test_fd_weights_textbook_values():
+    with open(os.path.join(GOLDEN, "fd_weights_textbook.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            kind, p, *w = line.split()
+            ref = [float(Fraction(v)) for v in w]
+            got = O.fd_weights_staggered(int(p)) if kind == "staggered" else O.fd_weights_nodal(int(p))
+            np.testing.assert_allclose(got, ref, rtol=1e-14)
+
+
+def test_large_order_weights_stay_finite():
+    for p in (64, 100, 128, 200):
+        for f in (O.fd_weights_nodal, O.fd_weights_staggered):
+            w = f(p)
+            assert np.all(np.isfinite(w)) and len(w) == p // 2
+            # first-moment condition holds at any order
+            off = np.arange(1, p // 2 + 1) - (0.5 if f is O.fd_weights_staggered else 0.0)
+            assert abs(np.sum(2 * off * w) - 1.0) < 1e-12
+
+
+def test_modified_k_second_order_is_textbook():
+    L, d = 24, 0.7
+    k = 2 * math.pi * np.fft.fftfreq(L, d)
+    nod = O.modified_k(L, d, 2, False)
+    stg = O.modified_k(L, d, 2, True)
+    ref_n = np.sin(k * d) / d
+    ref_s = 2 * np.sin(k * d / 2) / d
+    ref_n[L // 2] = 0.0
+    ref_s[L // 2] = 0.0
+    np.testing.assert_allclose(nod, ref_n, atol=1e-14)
+    np.testing.assert_allclose(stg, ref_s, atol=1e-14)
+
+
+def test_modified_k_converges_to_exact_with_order():
+    L, d = 64, 1.0
+    kex = O.k_exact(L, d)
+    band = np.abs(kex * d) <= 0.5 * math.pi
+    for staggered in (False, True):
+        errs = [np.max(np.abs(O.modified_k(L, d, p, staggered) - kex)[band]) for p in (2, 4, 8, 16, 32, 64, 100)]
+        assert all(b < a for a, b in zip(errs, errs[1:])), errs
+        assert errs[-1] < 1e-12
+    assert np.array_equal(O.modified_k(L, d, 0, False)[band], kex[band])
+    # Nyquist reading: zero for every order
+    for p in (0, 2, 32):
+        for st in (False, True):
+            assert O.modified_k(L, d, p, st)[L // 2] == 0.0
+
+
+def test_modified_k_is_odd():
+    for L in (20, 21, 48):
+        for p in (0, 4, 32):
+            for st in (False, True):
+                km = O.modified_k(L, 1.0, p, st)
+                neg = km[(-np.arange(L)) % L]
+                np.testing.assert_allclose(km, -neg, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# local FFTs against brute-force DFT
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(4, 6, 8), (5, 7, 11), (13, 3, 2), (2, 2, 6)])
+def test_r2c_matches_brute_force_dft(shape):
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(shape)
+    full = O.brute_dft3(f)
+    half = O.r2c(f)
+    np.testing.assert_allclose(half, full[:, :, : shape[2] // 2 + 1], atol=1e-11 * np.abs(full).max())
+    back = O.c2r(half, shape)
+    np.testing.assert_allclose(back, f, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 against the exact solution of the Maxwell ODE with constant J
+# --------------------------------------------------------------------------
+def _cross_matrix(k):
+    return np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]], dtype=complex)
+
+
+def _ode_solution(k, E, B, J, dt):
+    """dE/dt = i k x B - J, dB/dt = -i k x E (Sec. 2 Eq. 2 in Fourier space),
+    solved exactly with the matrix exponential of the augmented system."""
+    K = _cross_matrix(k)
+    M = np.zeros((7, 7), dtype=complex)
+    M[0:3, 3:6] = 1j * K
+    M[3:6, 0:3] = -1j * K
+    M[0:3, 6] = -J
+    y = scipy.linalg.expm(M * dt) @ np.concatenate([E, B, [1.0]])
+    return y[0:3], y[3:6]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_eq1_equals_exact_ode_flow(seed):
+    rng = np.random.default_rng(seed)
+    cases = [rng.normal(size=3) * s for s in (0.3, 1.0, 2.5)] + [np.zeros(3), np.array([1e-5, 0, 0])]
+    for k in cases:
+        E = rng.normal(size=3) + 1j * rng.normal(size=3)
+        B = rng.normal(size=3) + 1j * rng.normal(size=3)
+        J = rng.normal(size=3) + 1j * rng.normal(size=3)
+        kn = np.linalg.norm(k)
+        if kn > 0:                      # Eq. 1b assumes div B = 0
+            h = k / kn
+            B = B - h * (h @ B)
+        for dt in (0.5, 1.3, 7.0):
+            e1, b1 = O.eq1_update(tuple(E), tuple(B), tuple(J), tuple(k), dt)
+            e_ref, b_ref = _ode_solution(k, E, B, J, dt)
+            scale = max(1.0, np.abs(e_ref).max(), np.abs(b_ref).max())
+            np.testing.assert_allclose(np.array(e1), e_ref, atol=1e-12 * scale)
+            np.testing.assert_allclose(np.array(b1), b_ref, atol=1e-12 * scale)
+
+
+def test_eq1_k_zero_limit():
+    E, B, J = (1 + 2j, 3, -1j), (0.5, 0.25j, 2), (0.1, -0.2, 0.3j)
+    e1, b1 = O.eq1_update(E, B, J, (0.0, 0.0, 0.0), 0.4)
+    np.testing.assert_allclose(e1, np.array(E) - 0.4 * np.array(J), atol=1e-15)
+    np.testing.assert_allclose(b1, B, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# closed-form propagation and dispersion
+# --------------------------------------------------------------------------
+def _single_box(n, p, staggered=False, c_dt=0.5):
+    return I.custom("box", (n, n, n), ((n,), (n,), (n,)), 0, p, staggered=staggered, c_dt=c_dt)
+
+
+def _omega_exact_rational(k0, p, staggered):
+    if p == 0:
+        return k0
+    w = [float(v) for v in exact_weights(p, staggered)]
+    if staggered:
+        return sum(c * 2 * math.sin((2 * j + 1) * k0 / 2) for j, c in enumerate(w))
+    return sum(c * 2 * math.sin((j + 1) * k0) for j, c in enumerate(w))
+
+
+@pytest.mark.parametrize("p,staggered", [(0, False), (2, False), (8, False), (32, False),
+                                         (2, True), (4, True), (16, True)])
+def test_plane_wave_dispersion_closed_form(p, staggered):
+    """E_y = cos(k0 x - w t), B_z = cos(k0 x - w t) with w = |[k0]_p| (p = 0: w = k0)."""
+    n, m, steps, dt = 16, 3, 40, 0.5
+    wl = _single_box(n, p, staggered, dt)
+    k0 = 2 * math.pi * m / n
+    w = _omega_exact_rational(k0, p, staggered)
+    x = np.arange(n)[None, None, :] * np.ones((n, n, 1))
+    sx = {nm: I.STAGGER[nm][0] if staggered else 0.0 for nm in O.EB}
+    f = {nm: np.zeros((n, n, n)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    f["Ey"] = np.cos(k0 * (x + sx["Ey"]))
+    f["Bz"] = np.cos(k0 * (x + sx["Bz"]))
+    g = O.run(f, wl, steps)
+    t = steps * dt
+    np.testing.assert_allclose(g["Ey"], np.cos(k0 * (x + sx["Ey"]) - w * t), atol=2e-12)
+    np.testing.assert_allclose(g["Bz"], np.cos(k0 * (x + sx["Bz"]) - w * t), atol=2e-12)
+    for nm in ("Ex", "Ez", "Bx", "By"):
+        assert np.abs(g[nm]).max() < 1e-12
+
+
+def test_oblique_plane_wave_infinite_order():
+    n, dt, steps = 12, 0.9, 25
+    wl = _single_box(n, 0, False, dt)
+    kv = 2 * math.pi * np.array([2, -1, 3]) / n
+    kh = kv / np.linalg.norm(kv)
+    e = np.cross(kh, [0.3, 1.0, -0.2]); e /= np.linalg.norm(e)
+    b = np.cross(kh, e)
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    ph = kv[0] * x + kv[1] * y + kv[2] * z
+    f = {nm: np.zeros((n, n, n)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    for a in range(3):
+        f[O.EB[a]] = e[a] * np.cos(ph)
+        f[O.EB[3 + a]] = b[a] * np.cos(ph)
+    g = O.run(f, wl, steps)
+    ph2 = ph - np.linalg.norm(kv) * steps * dt
+    for a in range(3):
+        np.testing.assert_allclose(g[O.EB[a]], e[a] * np.cos(ph2), atol=2e-12)
+        np.testing.assert_allclose(g[O.EB[3 + a]], b[a] * np.cos(ph2), atol=2e-12)
+
+
+# --------------------------------------------------------------------------
+# invariants: energy (J = 0, transverse) and Gauss (charge-conserving J)
+# --------------------------------------------------------------------------
+def _transverse_random(n, p, staggered, rng):
+    """Random real E and B fields with div_p B = 0 (and div_p E = 0)."""
+    kmod, kex = O.local_kvectors((n, n, n), (1.0,) * 3, p, staggered)
+    out = {}
+    for grp in (O.EB[:3], O.EB[3:]):
+        spec = [O.r2c(rng.standard_normal((n, n, n))) for _ in range(3)]
+        km = np.sqrt(kmod[0] ** 2 + kmod[1] ** 2 + kmod[2] ** 2)
+        inv = np.where(km > 0, 1 / np.where(km > 0, km, 1), 0)
+        h = [kmod[a] * inv for a in range(3)]
+        d = sum(h[a] * spec[a] for a in range(3))
+        for a, nm in enumerate(grp):
+            F = spec[a] - h[a] * d
+            if staggered:
+                F = F / O._phase(nm, kex, (1.0,) * 3)
+            out[nm] = O.c2r(F, (n, n, n))
+    return out
+
+
+@pytest.mark.parametrize("p,staggered", [(0, False), (16, False), (6, True)])
+def test_vacuum_energy_conserved(p, staggered):
+    rng = np.random.default_rng(11)
+    n = 12
+    wl = _single_box(n, p, staggered, 0.7)
+    f = _transverse_random(n, p, staggered, rng)
+    for nm in ("Jx", "Jy", "Jz", "rho"):
+        f[nm] = np.zeros((n, n, n))
+    e0 = O.energy(f)
+    g = f
+    for _ in range(30):
+        g = O.step(g, wl)
+        assert abs(O.energy(g) - e0) / e0 < 1e-13
+
+
+@pytest.mark.parametrize("p,staggered", [(0, False), (12, False), (8, True)])
+def test_gauss_law_preserved_with_continuity(p, staggered):
+    rng = np.random.default_rng(5)
+    n, dt = 10, 0.6
+    wl = _single_box(n, p, staggered, dt)
+    f = {nm: rng.standard_normal((n, n, n)) for nm in O.EB + ("Jx", "Jy", "Jz")}
+    f.update(_transverse_random(n, p, staggered, rng))     # transverse B
+    f["Ex"] = f["Ex"] + rng.standard_normal((n, n, n))        # E with divergence
+    div_e = O.spectral_divergence(f["Ex"], f["Ey"], f["Ez"], (1.0,) * 3, p, staggered)
+    div_j = O.spectral_divergence(f["Jx"], f["Jy"], f["Jz"], (1.0,) * 3, p, staggered,
+                                  names=("Jx", "Jy", "Jz"))
+    rho_k = div_e.copy()                                     # Gauss satisfied at n = 0
+    g = dict(f)
+    for _ in range(8):
+        rho_k = rho_k - dt * div_j                           # continuity with the same [k]
+        g["rho"] = O.c2r(rho_k, (n, n, n))
+        gs = []
+        g = O.step(g, wl, gauss_out=gs)
+        res2, rho2 = gs[0]
+        assert res2 <= 1e-24 * max(rho2, 1.0), (res2, rho2)
+    # and div B stays zero
+    div_b = O.spectral_divergence(g["Bx"], g["By"], g["Bz"], (1.0,) * 3, p, staggered,
+                                  names=("Bx", "By", "Bz"))
+    assert np.abs(div_b).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# decomposition: exact special case and guard truncation (Sec. 3.2)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("p,staggered", [(0, False), (16, False), (8, True)])
+def test_local_equals_global_when_padded_box_is_one_period(p, staggered):
+    N = 16
+    wl = I.custom("sp", (N, N, N), ((8, 8),) * 3, 4, p, staggered=staggered, c_dt=0.45)
+    wl1 = I.custom("one", (N, N, N), ((N,),) * 3, 0, p, staggered=staggered, c_dt=0.45)
+    rng = np.random.default_rng(1)
+    f = {nm: rng.standard_normal((N, N, N)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    f.update(_transverse_random(N, p, staggered, rng))
+    a, b = f, f
+    for _ in range(5):
+        a = O.step(a, wl)
+        gp = O.global_push(b, p, (1.0,) * 3, 0.45, staggered)
+        b = dict(b, **gp)
+    assert O.rel_l2(a, b) < 1e-13
+    # one subdomain without guards is the global solver itself
+    assert O.rel_l2(O.run(f, wl1, 5), b) < 1e-13
+
+
+def test_guard_truncation_error_falls_with_guard_count():
+    N, p, steps = 48, 32, 6
+    glob = {k: v.numpy() for k, v in I.global_fields(I.custom("w", (N, N, N), ((24, 24),) * 3, 8, p,
+                                                             fields="wavepacket")).items()}
+    ref = glob
+    for _ in range(steps):
+        ref = dict(ref, **O.global_push(ref, p, (1.0,) * 3, 0.5, False))
+    errs = []
+    for ng in (2, 4, 8, 12):
+        wl = I.custom("w", (N, N, N), ((24, 24),) * 3, ng, p, fields="wavepacket")
+        errs.append(O.rel_l2(O.run(glob, wl, steps), ref))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-3 * errs[0]
+
+
+def test_unit_pulse_spurious_signal_stays_in_guards():
+    """3D analogue of Fig. 3: a unit pulse in the larger of two unequal
+    subdomains; after one push the local solution differs from the global one
+    mostly in the guard cells."""
+    Nx, N, ng, p = 48, 16, 8, 32
+    wl = I.custom("pulse", (Nx, N, N), ((30, 18), (N,), (N,)), ng, p, c_dt=0.5)
+    f = {nm: np.zeros((N, N, Nx)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    f["Ey"][N // 2, N // 2, 15] = 1.0
+    ref = O.global_push(f, p, (1.0,) * 3, 0.5, False)
+    for sd in wl.subs:
+        loc = {nm: O.extract_box(f[nm], sd.lo, sd.local, sd.ng) for nm in f}
+        out, _ = O.local_push(loc, sd.local, (1.0,) * 3, p, 0.5, False)
+        exp = {nm: O.extract_box(ref[nm], sd.lo, sd.local, sd.ng) for nm in O.EB}
+        g = sd.ng
+        valid = np.zeros(out["Ey"].shape, bool)
+        valid[g:-g, g:-g, g:-g] = True
+        dv = max(np.abs(out[nm] - exp[nm])[valid].max() for nm in O.EB)
+        dg = max(np.abs(out[nm] - exp[nm])[~valid].max() for nm in O.EB)
+        assert dv < 1e-2 * dg, (dv, dg)
+
+
+# --------------------------------------------------------------------------
+# exchange / decomposition bookkeeping
+# --------------------------------------------------------------------------
+def test_owner_map_tiles_every_workload():
+    for name in ("plain32", "yee64", "broadband256", "uneven48"):
+        wl = I.workload(name)
+        O.owner_map(wl.global_n, wl.subs)
+
+
+def test_extract_box_periodic_wrap():
+    G = np.arange(4 * 5 * 6, dtype=float).reshape(4, 5, 6)
+    box = O.extract_box(G, (0, 0, 0), (8, 9, 8), 1)
+    assert box[0, 0, 0] == G[-1, -1, -1]
+    assert box[1, 1, 1] == G[0, 0, 0]
+    assert box[1, 1, 7] == G[0, 0, 0]   # x wraps twice over a 6-wide axis
