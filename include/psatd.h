@@ -1,0 +1,154 @@
+/*
+ * psatd.h -- C ABI of libpsatd.so, a GB300 (sm_103a) local-FFT PSATD Maxwell
+ * solver after Vincenti & Vay, arXiv:1707.08500.
+ *
+ * The method (Sec. 3.2, Fig. 2a, Fig. 3): the periodic global grid is cut into
+ * subdomains; each is padded with n_g guard cells per side; every step each
+ * padded box is transformed with a local 3D real FFT, every Fourier mode is
+ * advanced analytically in time with Eq. 1a/1b (Sec. 3.1) using the order-p
+ * modified wavenumber, the box is transformed back, and the guard cells are
+ * replaced by the valid values of the subdomains that own them.
+ *
+ * Units: c = 1 and eps0 = 1 (Sec. 2, Eq. 2b reads D_t E = curl B - J).
+ *
+ * Memory model: the caller owns ALL device memory (field arenas and one
+ * workspace); the library never allocates device memory.  A plan owns only
+ * host metadata.  Every call that takes a stream only enqueues work on it: no
+ * synchronisation, no allocation, no host read of device data -- so those
+ * calls may be captured into a CUDA graph.  A plan is not thread-safe;
+ * different plans are independent.  psatd_set_workspace and psatd_set_coeffs
+ * are set-up calls: they copy metadata and tables to the workspace with
+ * blocking copies on the legacy default stream.
+ *
+ * Errors: every function returns PSATD_OK (0) or a negative status; no C++
+ * exception crosses the ABI.  psatd_last_error() gives a human-readable
+ * message for the last failing call on a plan.  Kernel launch failures are
+ * reported as PSATD_E_CUDA (checked with cudaPeekAtLastError, no sync).
+ */
+#ifndef PSATD_H
+#define PSATD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define PSATD_OK              0
+#define PSATD_E_ARG          -1  /* null pointer, bad enum, bad count          */
+#define PSATD_E_SHAPE        -2  /* decomposition does not tile the grid, odd p,
+                                    guard wider than supported, bad extent    */
+#define PSATD_E_NOMEM        -3  /* workspace smaller than psatd_workspace_bytes */
+#define PSATD_E_CUDA         -4  /* a CUDA runtime call or launch failed       */
+#define PSATD_E_UNSUPPORTED  -5  /* local length not a product of two factors
+                                    in 1..16, or odd local x length           */
+#define PSATD_E_STATE        -6  /* workspace or coefficients not set yet      */
+#define PSATD_E_TIMEOUT      -7  /* reserved: a bounded device wait gave up    */
+
+/* ---- plan flags ---------------------------------------------------------- */
+#define PSATD_F32            0x01 /* fields, spectra and FFTs in FP32; Eq. 1
+                                     coefficient tables built in FP64, stored FP32 */
+#define PSATD_F64            0x02 /* everything in FP64                          */
+#define PSATD_STAGGERED      0x04 /* Yee-staggered components (not in the paper):
+                                     order-p staggered modified wavenumber and
+                                     exact-k phase shifts to nodal position     */
+#define PSATD_GAUSS_DIAG     0x08 /* read rho and return per-subdomain FP64 sums
+                                     of |i[k].E~ - rho~|^2 and |rho~|^2            */
+#define PSATD_PLAIN          0x10 /* baseline schedule: one subdomain per launch,
+                                     guards refilled by a separate exchange
+                                     kernel (default: all subdomains batched in
+                                     one launch per stage, guard images written
+                                     by the inverse-FFT stage itself)            */
+
+/* One subdomain.  Its valid cells are the global indices [lo, lo+n) per axis
+ * (x, y, z); its local (padded) box is [lo-ng, lo+n+ng), of extent
+ * L = n + 2 ng per axis, read modulo the periodic global grid.
+ * order: even p >= 2, or 0 for the infinite-order limit (exact k). */
+typedef struct {
+    int32_t lo[3];
+    int32_t n[3];
+    int32_t ng;
+    int32_t order;
+} psatd_sub;
+
+/* Device pointers to the field arenas (one arena per component).  Every
+ * subdomain's local box is stored at the offset given by psatd_layout, as a
+ * dense [Lz][Ly][Lx] array (x fastest) of float (PSATD_F32) or double
+ * (PSATD_F64).  E and B hold the fields at time n on entry and n+1 on return;
+ * J (at n+1/2) and rho (at n+1, read only with PSATD_GAUSS_DIAG, else may be
+ * NULL) are read only.  Every pointer must be 16-byte aligned. */
+typedef struct {
+    void*       E[3];
+    void*       B[3];
+    const void* J[3];
+    const void* rho;
+} psatd_fields;
+
+typedef struct psatd_plan_s* psatd_plan_t;
+
+/* Build a plan (host only, no CUDA call).  global_n: periodic global grid
+ * (x, y, z).  Validated: the valid boxes tile the global grid exactly; every
+ * order is 0 or even; every local length is >= 4, the local x length is even,
+ * and every local length factors as n1*n2 with 1 <= n1, n2 <= 16; flags hold
+ * exactly one of PSATD_F32 / PSATD_F64.  Guard widths may exceed a
+ * neighbour's width (the guard is then filled from several owners). */
+int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
+                      const psatd_sub* subs, int32_t nsub, int32_t flags);
+
+/* Offset (in elements) of subdomain `sub` in every field arena, and its local
+ * extents (x, y, z).  Any output pointer may be NULL. */
+int psatd_layout(psatd_plan_t plan, int32_t sub, int64_t* offset_elems, int32_t local_n[3]);
+
+/* Number of elements each field arena must hold. */
+int psatd_arena_elems(psatd_plan_t plan, int64_t* elems);
+
+/* Bytes of device workspace the plan needs (spectra, coefficient tables,
+ * twiddles, descriptors, partial sums). */
+int psatd_workspace_bytes(psatd_plan_t plan, size_t* bytes);
+
+/* Attach caller-owned device workspace (256-byte aligned, at least
+ * psatd_workspace_bytes) and copy the plan's device metadata into it.  The
+ * memory stays owned by the caller and must outlive the plan's use. */
+int psatd_set_workspace(psatd_plan_t plan, void* dev_ptr, size_t bytes);
+
+/* Build the Eq. 1 coefficient tables (C, S, S/k, 1-C, (1-C)/k, S/k - dt, 1/k
+ * per mode, order-p modified wavenumbers, stagger phases, FFT twiddles) in
+ * FP64 on the host for c_dt = c*dt and cell sizes dx (x, y, z), and copy them
+ * to the workspace (rounded to FP32 for PSATD_F32).  Tables are shared by all
+ * subdomains with the same local shape and order.  Requires the workspace. */
+int psatd_set_coeffs(psatd_plan_t plan, double c_dt, const double dx[3]);
+
+/* One PSATD step of every subdomain (Sec. 3.2 with Eq. 1), followed by the
+ * guard replacement (Fig. 3 step 3), enqueued on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  E, B are updated in place.  On entry the
+ * guard cells must hold the owners' values (call psatd_exchange_guards once
+ * after loading the initial valid fields); on return they do again.
+ * gauss_dev: NULL, or a device array of 2*nsub doubles that receives, per
+ * subdomain, sum |i[k].E~^{n+1} - rho~|^2 and sum |rho~|^2 over the full
+ * spectrum of its padded box (unnormalised transforms); requires
+ * PSATD_GAUSS_DIAG. */
+int psatd_push(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev, void* stream);
+
+/* Copy every valid cell into each guard cell that images it (all 26
+ * neighbour directions, periodic wrap), for E and B only, on `stream`. */
+int psatd_exchange_guards(psatd_plan_t plan, const psatd_fields* fields, void* stream);
+
+/* Release the plan's host memory (the workspace stays the caller's). */
+int psatd_destroy(psatd_plan_t plan);
+
+/* Static text of a status code. */
+const char* psatd_status_string(int status);
+
+/* Message of the last failing call on `plan` ("" if none; valid until the
+ * next call on the plan). */
+const char* psatd_last_error(psatd_plan_t plan);
+
+/* Number of kernel launches one psatd_push enqueues for this plan. */
+int psatd_push_launches(psatd_plan_t plan, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSATD_H */

@@ -1,0 +1,64 @@
+// Internal descriptors shared by the host plan builder and the CUDA kernels.
+#pragma once
+#include <stdint.h>
+
+namespace psatd {
+
+constexpr int kMaxDft = 16;       // largest register DFT
+constexpr int kThreads = 256;     // threads per CTA of every stage kernel
+
+// One local FFT axis of length n = f1 * f2, done as two register stages.
+// Forward output (and inverse input) is in "position" order: frequency
+// k1 + f1*k2 sits at position k1*f2 + k2.
+struct AxisPlan {
+    int n, f1, f2;
+    int tw;          // offset of the n twiddles exp(-2 pi i m/n) in the pool
+};
+
+// Per subdomain, everything a stage kernel needs (device copy in workspace).
+struct SubDesc {
+    int L[3];            // local extents x, y, z
+    int nv[3];           // valid extents
+    int ng;
+    int lxh;             // Lx/2 + 1 (half-spectrum columns)
+    int pitch;           // complex row pitch of a plane in shared memory (odd)
+    int q;               // Ly * lxh: modes per z plane
+    AxisPlan ax;         // x: half length h = Lx/2 (complex FFT of packed pairs)
+    AxisPlan ay, az;
+    int tw_post;         // offset of exp(-2 pi i k/Lx), k = 0..Lx/2, in the pool
+    int pad0;
+    int64_t field_off;   // element offset of the local box in every field arena
+    int64_t spec_off;    // complex offset of this subdomain's spectra block
+    int64_t tab_coef;    // element offset of the 7 x (Lz*q) coefficient table
+    int64_t tab_k;       // element offset of [k] in position order: x (lxh), y (Ly), z (Lz)
+    int64_t tab_ph;      // complex offset of stagger phases (same layout), or -1
+    int seg_begin, seg_end;     // exchange segments whose source is this subdomain
+    int64_t itemA, itemB, itemC; // first work item of this subdomain in each stage
+    int chunkB;          // modes per pass-B chunk (M)
+    int pad1;
+};
+
+// A box of source valid cells copied into a destination local box.
+struct Segment {
+    int64_t dst_off;     // field-arena offset of the destination local box
+    int dLx, dLy;        // destination local extents x, y
+    int src;             // source subdomain
+    int dst;             // destination subdomain
+    int x0, y0, z0;      // first source local cell
+    int ex, ey, ez;      // extents
+    int dx, dy, dz;      // destination local = source local + (dx, dy, dz)
+    int identity;        // 1 when it is the source's own valid box (dst == src, no shift)
+    int64_t item;        // first exchange work item (one per z row of the segment)
+};
+
+// Pointers and counts common to every stage launch.
+struct LaunchCommon {
+    const void* subs; const void* segs; const void* tw; const void* tab; const void* tabc; void* spec;
+    void* eb[6]; const void* jr[4]; double* gauss_part;
+    int nsub, nseg, nf, staggered, own_only;
+};
+
+// Coefficient table component order (each Lz*q long, position order).
+enum { TAB_C = 0, TAB_S, TAB_SK, TAB_OMC, TAB_OMCK, TAB_DK, TAB_INVK, TAB_N };
+
+}  // namespace psatd

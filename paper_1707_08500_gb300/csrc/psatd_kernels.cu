@@ -1,0 +1,511 @@
+// CUDA kernels of the local-FFT PSATD push for sm_103a.
+//
+// One step of one padded subdomain (Sec. 3.2 of arXiv:1707.08500) is split
+// into three streaming stages over HBM:
+//
+//   pass A  per (subdomain, field, z plane): real x-FFT of the plane (as a
+//           half-length complex FFT of packed pairs plus the split step),
+//           then the y-FFT of every column; writes the plane's half spectrum.
+//   pass B  per (subdomain, chunk of M (ky,kx) modes): z-FFT of all fields,
+//           Eq. 1a/1b on every mode (Sec. 3.1), inverse z-FFT of E and B;
+//           writes back only the valid z planes.
+//   pass C  per (subdomain, E/B component, valid z plane): inverse y-FFT,
+//           inverse real x-FFT of the valid rows, then the guard replacement
+//           of Fig. 3 step 3 fused into the store: every valid cell is
+//           written to its own box and to every guard cell that images it.
+//
+// Every 1D transform of length n = f1*f2 runs in shared memory as two
+// in-place register stages (f1-point DFTs at stride f2, twiddle, f2-point
+// DFTs on contiguous blocks).  Forward transforms leave frequency k1 + f1*k2
+// at position k1*f2 + k2; the inverse consumes that order and returns natural
+// order, so spectra never need reordering: the host builds the per-mode
+// tables in the same position order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psatd_internal.h"
+#include "small_dft.cuh"
+
+namespace psatd {
+
+template <typename T>
+struct Args {
+    const SubDesc* subs;
+    const Segment* segs;
+    const cpx<T>* tw;       // twiddle pool
+    const T* tab;           // real tables (coefficients, wavenumbers)
+    const cpx<T>* tabc;     // complex tables (stagger phases)
+    cpx<T>* spec;           // spectra
+    T* eb[6];               // Ex Ey Ez Bx By Bz
+    const T* jr[4];         // Jx Jy Jz rho
+    double* gauss_part;     // 2 per pass-B item
+    int64_t item0, nitems;  // items handled by this launch
+    int nsub, nseg;
+    int nf;                 // fields transformed forward (9, or 10 with rho)
+    int staggered;
+    int own_only;           // pass C writes only the own valid box
+};
+
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T>
+__device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
+    const auto v = __ldg(reinterpret_cast<const typename vec2<T>::type*>(p));
+    return mk(v.x, v.y);
+}
+template <typename T>   // streaming (evict-first) load
+__device__ __forceinline__ cpx<T> ldcs_c(const cpx<T>* p) {
+    const auto v = __ldcs(reinterpret_cast<const typename vec2<T>::type*>(p));
+    return mk(v.x, v.y);
+}
+
+struct Batch {
+    int count;   // number of transforms
+    int inner;   // transforms per outer group
+    int s_in;    // stride between transforms of a group
+    int s_out;   // stride between groups
+    int es;      // stride between elements of one transform
+};
+
+__device__ __forceinline__ int boff(const Batch& b, int i) {
+    const int o = i / b.inner;
+    return (i - o * b.inner) * b.s_in + o * b.s_out;
+}
+
+// ---- shared-memory FFT stages ---------------------------------------------
+// Strided stage: each item loads R values at positions j + r*stride, does an
+// R-point DFT and (forward only) multiplies output r by w^{j r}; stores in place.
+template <int R, bool INV, bool TW, typename T>
+__device__ __forceinline__ void stage_strided(cpx<T>* sm, const Batch& bt, int stride,
+                                              const cpx<T>* __restrict__ tw) {
+    const int items = bt.count * stride;
+    const int es = bt.es * stride;
+    for (int it = threadIdx.x; it < items; it += kThreads) {
+        const int j = it / bt.count;
+        const int b = it - j * bt.count;
+        cpx<T>* p = sm + boff(bt, b) + j * bt.es;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r * es];
+        Dft<R, INV>::run(v);
+        if constexpr (TW) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], ldg_c(tw + j * r));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * es] = v[r];
+    }
+}
+
+// Block stage: each item k loads the R contiguous values k*R + r, does an
+// R-point DFT and (inverse only) multiplies output r by conj(w^{r k}).
+template <int R, bool INV, bool TW, typename T>
+__device__ __forceinline__ void stage_block(cpx<T>* sm, const Batch& bt, int nblk,
+                                            const cpx<T>* __restrict__ tw) {
+    const int items = bt.count * nblk;
+    for (int it = threadIdx.x; it < items; it += kThreads) {
+        const int k = it / bt.count;
+        const int b = it - k * bt.count;
+        cpx<T>* p = sm + boff(bt, b) + k * R * bt.es;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r * bt.es];
+        Dft<R, INV>::run(v);
+        if constexpr (TW) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], ldg_c(tw + r * k));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * bt.es] = v[r];
+    }
+}
+
+// natural order in -> position order out
+template <typename T>
+__device__ __forceinline__ void fft_fwd(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const cpx<T>* tw) {
+    const cpx<T>* w = tw + ax.tw;
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, false, true>(sm, bt, ax.f2, w); });
+    __syncthreads();
+    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, false, false>(sm, bt, ax.f1, w); });
+    __syncthreads();
+}
+
+// position order in -> natural order out (unnormalised)
+template <typename T>
+__device__ __forceinline__ void fft_inv(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const cpx<T>* tw) {
+    const cpx<T>* w = tw + ax.tw;
+    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, true, true>(sm, bt, ax.f1, w); });
+    __syncthreads();
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, true, false>(sm, bt, ax.f2, w); });
+    __syncthreads();
+}
+
+__device__ __forceinline__ int xpos(int k, const AxisPlan& a) { return (k % a.f1) * a.f2 + k / a.f1; }
+
+template <int STAGE>
+__device__ __forceinline__ int64_t stage_item(const SubDesc& d) {
+    return STAGE == 0 ? d.itemA : STAGE == 1 ? d.itemB : d.itemC;
+}
+
+template <int STAGE>
+__device__ __forceinline__ int find_sub(const SubDesc* __restrict__ subs, int nsub, int64_t item) {
+    int lo = 0, hi = nsub - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (stage_item<STAGE>(subs[mid]) <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
+    return f < 6 ? a.eb[f] : a.jr[f - 6];
+}
+
+// ---- pass A: x (real) and y forward transforms of one plane ---------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass_a(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+        const SubDesc& d = a.subs[find_sub<0>(a.subs, a.nsub, it)];
+        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
+        const int loc = int(it - d.itemA);
+        const int f = loc / Lz, z = loc - (loc / Lz) * Lz;
+        const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
+        const cpx<T>* src = reinterpret_cast<const cpx<T>*>(field_in(a, f) + d.field_off + int64_t(z) * Ly * Lx);
+        for (int i = threadIdx.x; i < Ly * h; i += kThreads) {
+            const int y = i / h;
+            sm[y * pitch + (i - y * h)] = ldcs_c(src + i);
+        }
+        __syncthreads();
+        // x: complex FFT of length h over the Ly rows
+        fft_fwd(sm, d.ax, Batch{Ly, Ly, pitch, 0, 1}, a.tw);
+        // split the packed transform into the half spectrum X[0..h]
+        const cpx<T>* wp = a.tw + d.tw_post;
+        const int npair = h / 2 + 1;
+        for (int i = threadIdx.x; i < Ly * npair; i += kThreads) {
+            const int k = i / Ly, y = i - k * Ly;
+            cpx<T>* p = sm + y * pitch;
+            if (k == 0) {
+                const cpx<T> z0 = p[0];
+                p[0] = mk(z0.x + z0.y, T(0));
+                p[h] = mk(z0.x - z0.y, T(0));
+            } else {
+                const int pa = xpos(k, d.ax), pb = xpos(h - k, d.ax);
+                const cpx<T> A = p[pa], Bc = conj(p[pb]);
+                const cpx<T> e = scale(A + Bc, T(0.5));
+                const cpx<T> dd = A - Bc;
+                const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);   // (A - conj B)/(2i)
+                const cpx<T> wo = cmul(ldg_c(wp + k), o);
+                p[pa] = e + wo;
+                if (pb != pa) p[pb] = conj(e - wo);
+            }
+        }
+        __syncthreads();
+        // y: complex FFT of length Ly over the lxh columns
+        fft_fwd(sm, d.ay, Batch{lxh, lxh, 1, 0, pitch}, a.tw);
+        cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
+        for (int i = threadIdx.x; i < d.q; i += kThreads) {
+            const int y = i / lxh;
+            dst[i] = sm[y * pitch + (i - y * lxh)];
+        }
+        __syncthreads();
+    }
+}
+
+// ---- pass B: z transforms and the Eq. 1 update -----------------------------
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kThreads / 32; ++i) s += red[i];
+    }
+    __syncthreads();
+    return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass_b(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ double red[2][kThreads / 32];
+    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+        const SubDesc& d = a.subs[find_sub<1>(a.subs, a.nsub, it)];
+        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
+        const int M = d.chunkB, Q = d.q, lxh = d.lxh;
+        const int q0 = int(it - d.itemB) * M;
+        const int mc = min(M, Q - q0);
+        const int nf = a.nf;
+        const int fs = Lz * M;                         // field stride in shared memory
+        cpx<T>* spec = a.spec + d.spec_off;
+        for (int i = threadIdx.x; i < nf * fs; i += kThreads) {
+            const int r = i / M, m = i - r * M;
+            const int f = r / Lz, z = r - f * Lz;
+            sm[i] = m < mc ? ldcs_c(spec + int64_t(f * Lz + z) * Q + q0 + m) : mk(T(0), T(0));
+        }
+        __syncthreads();
+        fft_fwd(sm, d.az, Batch{nf * M, M, 1, fs, M}, a.tw);
+
+        const int64_t NM = int64_t(Lz) * Q;
+        const T* __restrict__ tk = a.tab + d.tab_k;
+        const T Nfull = T(double(Lx) * double(Ly) * double(Lz));
+        double g_res = 0.0, g_rho = 0.0;
+        for (int i = threadIdx.x; i < fs; i += kThreads) {
+            const int zp = i / M, m = i - (i / M) * M;
+            if (m >= mc) continue;
+            const int q = q0 + m;
+            const int yp = q / lxh, xp = q - yp * lxh;
+            const T* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q;
+            const T C = __ldg(tb), S = __ldg(tb + NM), Sk = __ldg(tb + 2 * NM), omC = __ldg(tb + 3 * NM);
+            const T omCk = __ldg(tb + 4 * NM), Dk = __ldg(tb + 5 * NM), inv = __ldg(tb + 6 * NM);
+            const T kx = __ldg(tk + xp), ky = __ldg(tk + lxh + yp), kz = __ldg(tk + lxh + Ly + zp);
+            const T hx = kx * inv, hy = ky * inv, hz = kz * inv;
+            cpx<T>* p = sm + i;
+            cpx<T> E0 = p[0], E1 = p[fs], E2 = p[2 * fs];
+            cpx<T> B0 = p[3 * fs], B1 = p[4 * fs], B2 = p[5 * fs];
+            cpx<T> J0 = p[6 * fs], J1 = p[7 * fs], J2 = p[8 * fs];
+            cpx<T> px, py, pz;
+            if (a.staggered) {
+                const cpx<T>* ph = a.tabc + d.tab_ph;
+                px = ldg_c(ph + xp); py = ldg_c(ph + lxh + yp); pz = ldg_c(ph + lxh + Ly + zp);
+                const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
+                E0 = cmul(E0, px); E1 = cmul(E1, py); E2 = cmul(E2, pz);
+                J0 = cmul(J0, px); J1 = cmul(J1, py); J2 = cmul(J2, pz);
+                B0 = cmul(B0, pyz); B1 = cmul(B1, pxz); B2 = cmul(B2, pxy);
+            }
+            // khat x B, khat x E, khat x J, khat.E, khat.J
+            const cpx<T> hB0 = scale(B2, hy) - scale(B1, hz), hB1 = scale(B0, hz) - scale(B2, hx), hB2 = scale(B1, hx) - scale(B0, hy);
+            const cpx<T> hE0 = scale(E2, hy) - scale(E1, hz), hE1 = scale(E0, hz) - scale(E2, hx), hE2 = scale(E1, hx) - scale(E0, hy);
+            const cpx<T> hJ0 = scale(J2, hy) - scale(J1, hz), hJ1 = scale(J0, hz) - scale(J2, hx), hJ2 = scale(J1, hx) - scale(J0, hy);
+            const cpx<T> dE = scale(E0, hx) + scale(E1, hy) + scale(E2, hz);
+            const cpx<T> dJ = scale(J0, hx) + scale(J1, hy) + scale(J2, hz);
+            // Eq. 1a: E' = C E + i S khat x B - S/k J + (1-C) khat (khat.E) + khat (khat.J)(S/k - dt)
+            const cpx<T> lo = scale(dE, omC) + scale(dJ, Dk);
+            cpx<T> F0 = scale(E0, C) + scale(mul_i(hB0), S) - scale(J0, Sk) + scale(lo, hx);
+            cpx<T> F1 = scale(E1, C) + scale(mul_i(hB1), S) - scale(J1, Sk) + scale(lo, hy);
+            cpx<T> F2 = scale(E2, C) + scale(mul_i(hB2), S) - scale(J2, Sk) + scale(lo, hz);
+            // Eq. 1b: B' = C B - i S khat x E + i (1-C)/k khat x J
+            cpx<T> G0 = scale(B0, C) - scale(mul_i(hE0), S) + scale(mul_i(hJ0), omCk);
+            cpx<T> G1 = scale(B1, C) - scale(mul_i(hE1), S) + scale(mul_i(hJ1), omCk);
+            cpx<T> G2 = scale(B2, C) - scale(mul_i(hE2), S) + scale(mul_i(hJ2), omCk);
+            if (nf > 9) {
+                // Gauss residual i[k].E' - rho on the unnormalised spectrum
+                const cpx<T> rho = p[9 * fs];
+                const cpx<T> div = mul_i(scale(F0, kx) + scale(F1, ky) + scale(F2, kz));
+                const double rx = double(div.x) * double(Nfull) - double(rho.x);
+                const double ry = double(div.y) * double(Nfull) - double(rho.y);
+                const double wgt = (xp == 0 || xp == lxh - 1) ? 1.0 : 2.0;
+                g_res += wgt * (rx * rx + ry * ry);
+                g_rho += wgt * (double(rho.x) * double(rho.x) + double(rho.y) * double(rho.y));
+            }
+            if (a.staggered) {
+                const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
+                F0 = cmulc(F0, px); F1 = cmulc(F1, py); F2 = cmulc(F2, pz);
+                G0 = cmulc(G0, pyz); G1 = cmulc(G1, pxz); G2 = cmulc(G2, pxy);
+            }
+            p[0] = F0; p[fs] = F1; p[2 * fs] = F2;
+            p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
+        }
+        __syncthreads();
+        fft_inv(sm, d.az, Batch{6 * M, M, 1, fs, M}, a.tw);
+        const int ng = d.ng, nz = d.nv[2];
+        for (int i = threadIdx.x; i < 6 * nz * M; i += kThreads) {
+            const int r = i / M, m = i - r * M;
+            const int f = r / nz, zv = r - f * nz;
+            if (m < mc) {
+                const int z = ng + zv;
+                spec[int64_t(f * Lz + z) * Q + q0 + m] = sm[f * fs + z * M + m];
+            }
+        }
+        if (nf > 9) {
+            const double s1 = block_sum<T>(g_res, red[0]);
+            const double s2 = block_sum<T>(g_rho, red[1]);
+            if (threadIdx.x == 0) {
+                a.gauss_part[2 * it] = s1;
+                a.gauss_part[2 * it + 1] = s2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- pass C: inverse y and x transforms, fused guard replacement ------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass_c(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+        const int s = find_sub<2>(a.subs, a.nsub, it);
+        const SubDesc& d = a.subs[s];
+        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
+        const int nz = d.nv[2], ny = d.nv[1], ng = d.ng;
+        const int loc = int(it - d.itemC);
+        const int f = loc / nz, z = ng + (loc - (loc / nz) * nz);
+        const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
+        const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
+        for (int i = threadIdx.x; i < d.q; i += kThreads) {
+            const int y = i / lxh;
+            sm[y * pitch + (i - y * lxh)] = ldcs_c(src + i);
+        }
+        __syncthreads();
+        fft_inv(sm, d.ay, Batch{lxh, lxh, 1, 0, pitch}, a.tw);
+        // merge the half spectrum of the valid rows into the packed form
+        const cpx<T>* wp = a.tw + d.tw_post;
+        const int npair = h / 2 + 1;
+        cpx<T>* rows = sm + ng * pitch;
+        for (int i = threadIdx.x; i < ny * npair; i += kThreads) {
+            const int k = i / ny, y = i - k * ny;
+            cpx<T>* p = rows + y * pitch;
+            if (k == 0) {
+                const T x0 = p[0].x, xh = p[h].x;        // real parts only (C2R)
+                p[0] = mk(x0 + xh, x0 - xh);
+            } else {
+                const int pa = xpos(k, d.ax), pb = xpos(h - k, d.ax);
+                const cpx<T> A = p[pa], Bc = conj(p[pb]);
+                const cpx<T> e = A + Bc;
+                const cpx<T> o = cmulc(A - Bc, ldg_c(wp + k));
+                p[pa] = e + mul_i(o);
+                if (pb != pa) p[pb] = conj(e) + mul_i(conj(o));
+            }
+        }
+        __syncthreads();
+        fft_inv(rows, d.ax, Batch{ny, ny, pitch, 0, 1}, a.tw);
+        // store the valid cells of this plane to every box that holds them
+        T* out = a.eb[f];
+        const T* rp = reinterpret_cast<const T*>(sm);
+        for (int g = d.seg_begin; g < d.seg_end; ++g) {
+            const Segment& sg = a.segs[g];
+            if (a.own_only && !sg.identity) continue;
+            if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
+            T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.dy) * sg.dLx + sg.dx;
+            const int cnt = sg.ex * sg.ey;
+            for (int i = threadIdx.x; i < cnt; i += kThreads) {
+                const int yy = i / sg.ex;
+                const int y = sg.y0 + yy, x = sg.x0 + (i - yy * sg.ex);
+                __stcs(dst + int64_t(y) * sg.dLx + x, rp[y * 2 * pitch + x]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- standalone guard exchange ---------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
+    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+        int lo = 0, hi = a.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.segs[mid].item <= it) lo = mid; else hi = mid - 1;
+        }
+        const Segment& sg = a.segs[lo];
+        const SubDesc& sd = a.subs[sg.src];
+        const int z = sg.z0 + int(it - sg.item);
+        const int cnt = sg.ex * sg.ey;
+        for (int f = 0; f < 6; ++f) {
+            T* fld = a.eb[f];
+            const T* src = fld + sd.field_off + (int64_t(z) * sd.L[1] + sg.y0) * sd.L[0] + sg.x0;
+            T* dst = fld + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
+            for (int i = threadIdx.x; i < cnt; i += kThreads) {
+                const int yy = i / sg.ex, xx = i - yy * sg.ex;
+                dst[int64_t(yy) * sg.dLx + xx] = src[int64_t(yy) * sd.L[0] + xx];
+            }
+        }
+    }
+}
+
+// ---- per-subdomain reduction of the Gauss partial sums ----------------------
+__global__ void k_gauss_reduce(const SubDesc* __restrict__ subs, int nsub, const double* __restrict__ part,
+                               double* __restrict__ out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (w >= nsub) return;
+    const int64_t b = subs[w].itemB;
+    const int64_t end = b + (int64_t(subs[w].q) + subs[w].chunkB - 1) / subs[w].chunkB;
+    double s1 = 0, s2 = 0;
+    for (int64_t i = b + l; i < end; i += 32) { s1 += part[2 * i]; s2 += part[2 * i + 1]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (l == 0) { out[2 * w] = s1; out[2 * w + 1] = s2; }
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+template <typename T>
+static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
+    Args<T> a;
+    a.subs = static_cast<const SubDesc*>(c.subs);
+    a.segs = static_cast<const Segment*>(c.segs);
+    a.tw = static_cast<const cpx<T>*>(c.tw);
+    a.tab = static_cast<const T*>(c.tab);
+    a.tabc = static_cast<const cpx<T>*>(c.tabc);
+    a.spec = static_cast<cpx<T>*>(c.spec);
+    for (int i = 0; i < 6; ++i) a.eb[i] = static_cast<T*>(c.eb[i]);
+    for (int i = 0; i < 4; ++i) a.jr[i] = static_cast<const T*>(c.jr[i]);
+    a.gauss_part = c.gauss_part;
+    a.item0 = item0;
+    a.nitems = nitems;
+    a.nsub = c.nsub;
+    a.nseg = c.nseg;
+    a.nf = c.nf;
+    a.staggered = c.staggered;
+    a.own_only = c.own_only;
+    return a;
+}
+
+static unsigned grid_for(int64_t n) { return unsigned(n < 2147483647 ? n : 2147483647); }
+
+template <typename T>
+static cudaError_t set_smem_attr(const void* fn, int bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T>
+cudaError_t launch_stage(int stage, const LaunchCommon& c, int64_t item0, int64_t nitems, int smem, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    Args<T> a = make_args<T>(c, item0, nitems);
+    const void* fn = stage == 0 ? (const void*)k_pass_a<T> : stage == 1 ? (const void*)k_pass_b<T>
+                   : stage == 2 ? (const void*)k_pass_c<T> : (const void*)k_exchange<T>;
+    cudaError_t e = set_smem_attr<T>(fn, smem);
+    if (e != cudaSuccess) return e;
+    switch (stage) {
+        case 0: k_pass_a<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
+        case 1: k_pass_b<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
+        case 2: k_pass_c<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
+        default: k_exchange<T><<<grid_for(nitems), kThreads, 0, st>>>(a); break;
+    }
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_gauss_reduce(const void* subs, int nsub, const double* part, double* out, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (nsub * 32 + threads - 1) / threads;
+    k_gauss_reduce<<<blocks, threads, 0, st>>>(static_cast<const SubDesc*>(subs), nsub, part, out);
+    return cudaPeekAtLastError();
+}
+
+template cudaError_t launch_stage<float>(int, const LaunchCommon&, int64_t, int64_t, int, cudaStream_t);
+template cudaError_t launch_stage<double>(int, const LaunchCommon&, int64_t, int64_t, int, cudaStream_t);
+
+}  // namespace psatd
+
+// entry points used by the host plan code (C++ linkage inside the library)
+namespace psatd {
+cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
+    return launch_stage<float>(stage, c, i0, n, smem, s);
+}
+cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
+    return launch_stage<double>(stage, c, i0, n, smem, s);
+}
+}  // namespace psatd

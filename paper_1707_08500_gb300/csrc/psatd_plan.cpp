@@ -1,0 +1,614 @@
+// Host side of libpsatd.so: plan validation, decomposition bookkeeping, the
+// FP64 construction of the Eq. 1 tables (Sec. 3.1 of arXiv:1707.08500) and
+// the C ABI declared in include/psatd.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "psatd.h"
+#include "psatd_internal.h"
+
+namespace psatd {
+cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
+cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
+cudaError_t launch_gauss_reduce(const void* subs, int nsub, const double* part, double* out, cudaStream_t st);
+}  // namespace psatd
+
+using namespace psatd;
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// exp(-2 pi i m / n) with an exact octant reduction of the rational angle
+cd unit_root(long m, long n) {
+    long r = ((m % n) + n) % n;
+    // angle = 2 pi r / n in [0, 2 pi); reduce to [0, pi/4] by symmetry
+    long num = 8 * r;            // angle = (pi/4) * num / n
+    long oct = num / n;
+    long rem = num - oct * n;    // angle = (pi/4)(oct + rem/n)
+    double phi = (kPi / 4) * double(rem) / double(n);
+    double c, s;
+    // angle = oct*pi/4 + phi; evaluate with the reflection that keeps the
+    // argument of sin/cos in [0, pi/4]
+    switch (oct) {
+        case 0: c = std::cos(phi); s = std::sin(phi); break;
+        case 1: { double t = kPi / 4 - phi; c = std::sin(t); s = std::cos(t); break; }
+        case 2: c = -std::sin(phi); s = std::cos(phi); break;
+        case 3: { double t = kPi / 4 - phi; c = -std::cos(t); s = std::sin(t); break; }
+        case 4: c = -std::cos(phi); s = -std::sin(phi); break;
+        case 5: { double t = kPi / 4 - phi; c = -std::sin(t); s = -std::cos(t); break; }
+        case 6: c = std::sin(phi); s = -std::cos(phi); break;
+        default: { double t = kPi / 4 - phi; c = std::cos(t); s = -std::sin(t); break; }
+    }
+    return cd(c, -s);
+}
+
+// centred nodal weights w_j of f' ~ sum_j w_j (f_{+j} - f_{-j})/du (order p)
+std::vector<double> weights_nodal(int p) {
+    int m = p / 2;
+    std::vector<double> w(m);
+    w[0] = double(m) / (m + 1.0);
+    for (int j = 1; j < m; ++j) w[j] = -w[j - 1] * j * (m - j) / ((j + 1.0) * (m + j + 1.0));
+    return w;
+}
+
+// staggered weights c_j of f' ~ sum_j c_j (f_{+(j-1/2)} - f_{-(j-1/2)})/du
+std::vector<double> weights_staggered(int p) {
+    int m = p / 2;
+    double lg = 0;
+    for (int i = 1; i <= m; ++i) lg += std::log(2.0 * i - 1.0);
+    double lc1 = 2 * lg - std::lgamma(double(m)) - std::lgamma(double(m) + 1) - (m - 1) * std::log(4.0);
+    std::vector<double> c(m);
+    c[0] = std::exp(lc1);
+    for (int j = 1; j < m; ++j) c[j] = -c[j - 1] * double(2 * j - 1) * (2 * j - 1) * (m - j) / (double(2 * j + 1) * (2 * j + 1) * (m + j));
+    return c;
+}
+
+// exact wavenumber of DFT index i of an L-point axis; L/2 carries -pi/du
+double kexact(int i, int L, double du) {
+    int nn = (i < (L + 1) / 2) ? i : i - L;
+    return 2.0 * kPi * nn / (L * du);
+}
+
+// order-p modified wavenumber (Sec. 3.1); zero at the Nyquist index
+double kmod(int i, int L, double du, int p, bool stag) {
+    if (L % 2 == 0 && i == L / 2) return 0.0;
+    double k = kexact(i, L, du);
+    if (p == 0) return k;
+    double s = 0;
+    if (!stag) {
+        std::vector<double> w = weights_nodal(p);
+        for (size_t j = 0; j < w.size(); ++j) s += w[j] * std::sin((j + 1) * k * du) / (du / 2);
+    } else {
+        std::vector<double> c = weights_staggered(p);
+        for (size_t j = 0; j < c.size(); ++j) s += c[j] * 2.0 * std::sin((2.0 * j + 1.0) * k * du / 2) / du;
+    }
+    return s;
+}
+
+bool factor(int n, int& f1, int& f2) {
+    // prefer the most balanced split with both factors in 1..16
+    int best = -1;
+    for (int a = 1; a <= kMaxDft; ++a) {
+        if (n % a) continue;
+        int b = n / a;
+        if (b > kMaxDft) continue;
+        int score = std::min(a, b) * 64 + a;   // balanced first, then larger f1
+        if (score > best) { best = score; f1 = a; f2 = b; }
+    }
+    return best >= 0;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct psatd_plan_s {
+    int flags = 0;
+    int gn[3] = {0, 0, 0};
+    std::vector<psatd_sub> subs;
+    std::vector<SubDesc> desc;
+    std::vector<Segment> segs;
+    int64_t arena_elems = 0;
+    int nf = 9;
+    bool f64 = false, stag = false, plain = false, diag = false;
+    // twiddle pool: (n) -> offset; post twiddles: (Lx) -> offset
+    std::map<int, int> tw_off, post_off;
+    int64_t n_tw = 0;
+    // table sets keyed by (Lx, Ly, Lz, p, fx1, fy1, fz1)
+    struct TabKey { int Lx, Ly, Lz, p, f1x, f1y, f1z; bool operator<(const TabKey& o) const {
+        return std::tie(Lx, Ly, Lz, p, f1x, f1y, f1z) < std::tie(o.Lx, o.Ly, o.Lz, o.p, o.f1x, o.f1y, o.f1z); } };
+    std::map<TabKey, int> tab_index;
+    std::vector<TabKey> tab_keys;
+    std::vector<int64_t> tab_coef_off, tab_k_off, tab_ph_off;
+    int64_t n_tab = 0, n_tabc = 0;
+    int64_t items[3] = {0, 0, 0};
+    int64_t exch_items = 0;
+    int smemA = 0, smemB = 0, smemC = 0;
+    // workspace layout (bytes)
+    size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_spec = 0, ws_need = 0;
+    int64_t spec_elems = 0;
+    char* ws = nullptr;
+    size_t ws_size = 0;
+    bool coeffs = false;
+    std::string err;
+};
+
+static int fail(psatd_plan_s* p, int code, const std::string& msg) {
+    if (p) p->err = msg;
+    return code;
+}
+
+static int cuda_fail(psatd_plan_s* p, cudaError_t e, const char* where) {
+    return fail(p, PSATD_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" {
+
+const char* psatd_status_string(int s) {
+    switch (s) {
+        case PSATD_OK: return "ok";
+        case PSATD_E_ARG: return "invalid argument";
+        case PSATD_E_SHAPE: return "invalid decomposition or shape";
+        case PSATD_E_NOMEM: return "workspace too small";
+        case PSATD_E_CUDA: return "CUDA error";
+        case PSATD_E_UNSUPPORTED: return "unsupported local length";
+        case PSATD_E_STATE: return "workspace or coefficients not set";
+        case PSATD_E_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* psatd_last_error(psatd_plan_t p) { return p ? p->err.c_str() : "null plan"; }
+
+int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub, int32_t flags) {
+    if (!out || !global_n || !subs || nsub <= 0) return PSATD_E_ARG;
+    *out = nullptr;
+    psatd_plan_s* p = new (std::nothrow) psatd_plan_s();
+    if (!p) return PSATD_E_ARG;
+    auto bad = [&](int code, const std::string& m) { int c = fail(p, code, m); delete p; return c; };
+    int prec = flags & (PSATD_F32 | PSATD_F64);
+    if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
+    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN))
+        return bad(PSATD_E_ARG, "unknown flag bits");
+    p->flags = flags;
+    p->f64 = prec == PSATD_F64;
+    p->stag = flags & PSATD_STAGGERED;
+    p->plain = flags & PSATD_PLAIN;
+    p->diag = flags & PSATD_GAUSS_DIAG;
+    p->nf = p->diag ? 10 : 9;
+    for (int a = 0; a < 3; ++a) {
+        if (global_n[a] <= 0) return bad(PSATD_E_SHAPE, "global extents must be positive");
+        p->gn[a] = global_n[a];
+    }
+    p->subs.assign(subs, subs + nsub);
+    // --- tiling: inside the grid, disjoint, volumes add up -------------------
+    int64_t vol = 0;
+    for (int s = 0; s < nsub; ++s) {
+        const psatd_sub& d = subs[s];
+        for (int a = 0; a < 3; ++a) {
+            if (d.n[a] <= 0 || d.lo[a] < 0 || d.lo[a] + d.n[a] > global_n[a])
+                return bad(PSATD_E_SHAPE, "subdomain " + std::to_string(s) + " leaves the global grid");
+        }
+        if (d.ng < 0) return bad(PSATD_E_SHAPE, "negative guard width");
+        if (d.order < 0 || d.order % 2) return bad(PSATD_E_SHAPE, "order must be 0 or even");
+        vol += int64_t(d.n[0]) * d.n[1] * d.n[2];
+    }
+    if (vol != int64_t(global_n[0]) * global_n[1] * global_n[2])
+        return bad(PSATD_E_SHAPE, "subdomain volumes do not add up to the global grid");
+    {
+        // sweep: sort by x-low and test overlaps of boxes (O(n^2) worst case, plan time only)
+        std::vector<int> ord(nsub);
+        for (int i = 0; i < nsub; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return subs[a].lo[0] < subs[b].lo[0]; });
+        for (int ii = 0; ii < nsub; ++ii) {
+            const psatd_sub& A = subs[ord[ii]];
+            for (int jj = ii + 1; jj < nsub; ++jj) {
+                const psatd_sub& B = subs[ord[jj]];
+                if (B.lo[0] >= A.lo[0] + A.n[0]) break;
+                bool ov = true;
+                for (int a = 0; a < 3; ++a)
+                    ov = ov && (A.lo[a] < B.lo[a] + B.n[a]) && (B.lo[a] < A.lo[a] + A.n[a]);
+                if (ov) return bad(PSATD_E_SHAPE, "subdomains " + std::to_string(ord[ii]) + " and " + std::to_string(ord[jj]) + " overlap");
+            }
+        }
+    }
+    // --- per-subdomain descriptors -------------------------------------------
+    const int64_t esz = p->f64 ? 8 : 4;
+    p->desc.resize(nsub);
+    int64_t aoff = 0;
+    for (int s = 0; s < nsub; ++s) {
+        const psatd_sub& u = subs[s];
+        SubDesc& d = p->desc[s];
+        std::memset(&d, 0, sizeof(d));
+        for (int a = 0; a < 3; ++a) { d.nv[a] = u.n[a]; d.L[a] = u.n[a] + 2 * u.ng; }
+        d.ng = u.ng;
+        if (d.L[0] % 2 || d.L[0] < 2) return bad(PSATD_E_UNSUPPORTED, "local x length must be even");
+        int h = d.L[0] / 2;
+        if (!factor(h, d.ax.f1, d.ax.f2) || !factor(d.L[1], d.ay.f1, d.ay.f2) || !factor(d.L[2], d.az.f1, d.az.f2))
+            return bad(PSATD_E_UNSUPPORTED, "subdomain " + std::to_string(s) + ": local length is not a product of two factors <= 16");
+        d.ax.n = h; d.ay.n = d.L[1]; d.az.n = d.L[2];
+        d.lxh = h + 1;
+        d.pitch = d.lxh | 1;
+        d.q = d.L[1] * d.lxh;
+        d.field_off = aoff;
+        int64_t cells = int64_t(d.L[0]) * d.L[1] * d.L[2];
+        aoff += align_up(cells, 64);            // 256-byte aligned boxes (FP32), 512 (FP64)
+    }
+    p->arena_elems = aoff;
+    // --- twiddles -------------------------------------------------------------
+    auto add_tw = [&](int n) {
+        auto it = p->tw_off.find(n);
+        if (it != p->tw_off.end()) return it->second;
+        int off = int(p->n_tw);
+        p->tw_off[n] = off;
+        p->n_tw += n;
+        return off;
+    };
+    for (auto& d : p->desc) {
+        d.ax.tw = add_tw(d.ax.n);
+        d.ay.tw = add_tw(d.ay.n);
+        d.az.tw = add_tw(d.az.n);
+    }
+    for (auto& d : p->desc) {
+        auto it = p->post_off.find(d.L[0]);
+        if (it == p->post_off.end()) {
+            p->post_off[d.L[0]] = int(p->n_tw);
+            p->n_tw += d.L[0] / 2 + 1;
+        }
+        d.tw_post = p->post_off[d.L[0]];
+    }
+    // --- coefficient tables, one set per (shape, order, factorisation) ----------
+    for (int s = 0; s < nsub; ++s) {
+        SubDesc& d = p->desc[s];
+        psatd_plan_s::TabKey k{d.L[0], d.L[1], d.L[2], subs[s].order, d.ax.f1, d.ay.f1, d.az.f1};
+        auto it = p->tab_index.find(k);
+        int ti;
+        if (it == p->tab_index.end()) {
+            ti = int(p->tab_keys.size());
+            p->tab_index[k] = ti;
+            p->tab_keys.push_back(k);
+            int64_t nm = int64_t(d.L[2]) * d.q;
+            p->tab_coef_off.push_back(p->n_tab);
+            p->n_tab += align_up(TAB_N * nm, 64);
+            p->tab_k_off.push_back(p->n_tab);
+            p->n_tab += align_up(d.lxh + d.L[1] + d.L[2], 64);
+            p->tab_ph_off.push_back(p->stag ? p->n_tabc : -1);
+            if (p->stag) p->n_tabc += align_up(d.lxh + d.L[1] + d.L[2], 32);
+        } else {
+            ti = it->second;
+        }
+        d.tab_coef = p->tab_coef_off[ti];
+        d.tab_k = p->tab_k_off[ti];
+        d.tab_ph = p->tab_ph_off[ti];
+    }
+    // --- pass-B chunk, shared memory, work items --------------------------------
+    const int csz = p->f64 ? 16 : 8;
+    int64_t iA = 0, iB = 0, iC = 0, spec = 0, maxspec = 0;
+    for (int s = 0; s < nsub; ++s) {
+        SubDesc& d = p->desc[s];
+        int M = p->f64 ? 4 : 8;
+        while (M > 1 && int64_t(p->nf) * d.L[2] * M * csz > 100 * 1024) M /= 2;
+        d.chunkB = M;
+        p->smemA = std::max(p->smemA, d.L[1] * d.pitch * csz);
+        p->smemC = p->smemA;
+        p->smemB = std::max(p->smemB, p->nf * d.L[2] * M * csz);
+        d.itemA = iA; iA += int64_t(p->nf) * d.L[2];
+        d.itemB = iB; iB += (d.q + M - 1) / M;
+        d.itemC = iC; iC += 6 * int64_t(d.nv[2]);
+        int64_t sp = int64_t(p->nf) * d.L[2] * d.q;
+        d.spec_off = p->plain ? 0 : spec;
+        spec += int64_t(align_up(sp, 32));
+        maxspec = std::max<int64_t>(maxspec, int64_t(align_up(sp, 32)));
+    }
+    p->items[0] = iA; p->items[1] = iB; p->items[2] = iC;
+    p->spec_elems = p->plain ? maxspec : spec;
+    if (std::max(p->smemA, p->smemB) > 227 * 1024)
+        return bad(PSATD_E_UNSUPPORTED, "a local plane does not fit in shared memory");
+    // --- exchange segments (source valid box -> destination local box) ----------
+    for (int s = 0; s < nsub; ++s) {
+        p->desc[s].seg_begin = int(p->segs.size());
+        const psatd_sub& S = subs[s];
+        for (int dd = 0; dd < nsub; ++dd) {
+            const psatd_sub& D = subs[dd];
+            const SubDesc& Dd = p->desc[dd];
+            // per axis: list of (shift, lo, hi) intersections in global unwrapped coords
+            std::vector<std::tuple<long, long, long>> ax[3];
+            for (int a = 0; a < 3; ++a) {
+                long N = global_n[a];
+                long b0 = long(D.lo[a]) - D.ng, b1 = long(D.lo[a]) + D.n[a] + D.ng;
+                long tmin = (long)std::floor(double(b0 - (S.lo[a] + S.n[a])) / N) - 1;
+                long tmax = (long)std::ceil(double(b1 - S.lo[a]) / N) + 1;
+                for (long t = tmin; t <= tmax; ++t) {
+                    long a0 = S.lo[a] + t * N, a1 = S.lo[a] + S.n[a] + t * N;
+                    long lo = std::max(a0, b0), hi = std::min(a1, b1);
+                    if (lo < hi) ax[a].emplace_back(t, lo, hi);
+                }
+            }
+            for (auto& X : ax[0]) for (auto& Y : ax[1]) for (auto& Z : ax[2]) {
+                Segment g;
+                std::memset(&g, 0, sizeof(g));
+                g.src = s; g.dst = dd;
+                g.dst_off = Dd.field_off;
+                g.dLx = Dd.L[0]; g.dLy = Dd.L[1];
+                long t[3] = {std::get<0>(X), std::get<0>(Y), std::get<0>(Z)};
+                long lo[3] = {std::get<1>(X), std::get<1>(Y), std::get<1>(Z)};
+                long hi[3] = {std::get<2>(X), std::get<2>(Y), std::get<2>(Z)};
+                int x0[3], ext[3], off[3];
+                for (int a = 0; a < 3; ++a) {
+                    long src_origin = S.lo[a] + t[a] * global_n[a] - S.ng;   // global coord of source local 0
+                    long dst_origin = long(D.lo[a]) - D.ng;
+                    x0[a] = int(lo[a] - src_origin);
+                    ext[a] = int(hi[a] - lo[a]);
+                    off[a] = int(src_origin - dst_origin);
+                }
+                g.x0 = x0[0]; g.y0 = x0[1]; g.z0 = x0[2];
+                g.ex = ext[0]; g.ey = ext[1]; g.ez = ext[2];
+                g.dx = off[0]; g.dy = off[1]; g.dz = off[2];
+                g.identity = (dd == s && t[0] == 0 && t[1] == 0 && t[2] == 0) ? 1 : 0;
+                p->segs.push_back(g);
+            }
+        }
+        p->desc[s].seg_end = int(p->segs.size());
+    }
+    int64_t ei = 0;
+    for (auto& g : p->segs) {
+        g.item = ei;
+        if (!g.identity) ei += g.ez;
+    }
+    p->exch_items = ei;
+    // --- workspace layout ------------------------------------------------------
+    size_t o = 0;
+    p->off_desc = o; o = align_up(o + sizeof(SubDesc) * p->desc.size(), 256);
+    p->off_seg = o; o = align_up(o + sizeof(Segment) * p->segs.size(), 256);
+    p->off_tw = o; o = align_up(o + size_t(p->n_tw) * 2 * esz, 256);
+    p->off_tab = o; o = align_up(o + size_t(p->n_tab) * esz, 256);
+    p->off_tabc = o; o = align_up(o + size_t(std::max<int64_t>(p->n_tabc, 1)) * 2 * esz, 256);
+    p->off_gauss = o; o = align_up(o + size_t(std::max<int64_t>(p->items[1], 1)) * 2 * sizeof(double), 256);
+    p->off_spec = o; o = align_up(o + size_t(p->spec_elems) * 2 * esz, 256);
+    p->ws_need = o;
+    *out = p;
+    return PSATD_OK;
+}
+
+int psatd_layout(psatd_plan_t p, int32_t sub, int64_t* offset_elems, int32_t local_n[3]) {
+    if (!p) return PSATD_E_ARG;
+    if (sub < 0 || sub >= int(p->desc.size())) return fail(p, PSATD_E_ARG, "subdomain index out of range");
+    if (offset_elems) *offset_elems = p->desc[sub].field_off;
+    if (local_n) for (int a = 0; a < 3; ++a) local_n[a] = p->desc[sub].L[a];
+    return PSATD_OK;
+}
+
+int psatd_arena_elems(psatd_plan_t p, int64_t* n) {
+    if (!p || !n) return PSATD_E_ARG;
+    *n = p->arena_elems;
+    return PSATD_OK;
+}
+
+int psatd_workspace_bytes(psatd_plan_t p, size_t* b) {
+    if (!p || !b) return PSATD_E_ARG;
+    *b = p->ws_need;
+    return PSATD_OK;
+}
+
+int psatd_push_launches(psatd_plan_t p, int32_t* n) {
+    if (!p || !n) return PSATD_E_ARG;
+    int nsub = int(p->desc.size());
+    *n = p->plain ? 3 * nsub + (p->exch_items > 0 ? 1 : 0) : 3;
+    if (p->diag) *n += 1;
+    return PSATD_OK;
+}
+
+int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
+    if (!p || !dev) return PSATD_E_ARG;
+    if (reinterpret_cast<uintptr_t>(dev) % 256) return fail(p, PSATD_E_ARG, "workspace must be 256-byte aligned");
+    if (bytes < p->ws_need) return fail(p, PSATD_E_NOMEM, "workspace smaller than psatd_workspace_bytes");
+    p->ws = static_cast<char*>(dev);
+    p->ws_size = bytes;
+    p->coeffs = false;
+    cudaError_t e = cudaMemcpy(p->ws + p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy descriptors"); }
+    if (!p->segs.empty()) {
+        e = cudaMemcpy(p->ws + p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy segments"); }
+    }
+    // twiddles exp(-2 pi i m/n) and the real-split twiddles exp(-2 pi i k/Lx)
+    std::vector<cd> tw(size_t(p->n_tw));
+    for (auto& kv : p->tw_off)
+        for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
+    for (auto& kv : p->post_off)
+        for (int k = 0; k <= kv.first / 2; ++k) tw[kv.second + k] = unit_root(k, kv.first);
+    if (p->f64) {
+        e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size() * sizeof(cd), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> t32(tw.size() * 2);
+        for (size_t i = 0; i < tw.size(); ++i) { t32[2 * i] = float(tw[i].real()); t32[2 * i + 1] = float(tw[i].imag()); }
+        e = cudaMemcpy(p->ws + p->off_tw, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
+    return PSATD_OK;
+}
+
+int psatd_set_coeffs(psatd_plan_t p, double c_dt, const double dx[3]) {
+    if (!p || !dx) return PSATD_E_ARG;
+    if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
+    if (!(c_dt == c_dt) || !(dx[0] > 0 && dx[1] > 0 && dx[2] > 0)) return fail(p, PSATD_E_ARG, "bad c_dt or dx");
+    std::vector<double> tab(size_t(p->n_tab), 0.0);
+    std::vector<cd> tabc(size_t(std::max<int64_t>(p->n_tabc, 1)));
+    for (size_t ti = 0; ti < p->tab_keys.size(); ++ti) {
+        const auto& key = p->tab_keys[ti];
+        const int L[3] = {key.Lx, key.Ly, key.Lz};
+        const int h = L[0] / 2, lxh = h + 1, q = L[1] * lxh;
+        const int f1[3] = {key.f1x, key.f1y, key.f1z};
+        const int n[3] = {h, L[1], L[2]};
+        // natural index held at each position of an axis (position order of the
+        // forward transforms: frequency k1 + f1 k2 at position k1 f2 + k2)
+        std::vector<int> nat[3];
+        for (int a = 0; a < 3; ++a) {
+            int f2 = n[a] / f1[a];
+            int len = a == 0 ? lxh : n[a];
+            nat[a].resize(len);
+            for (int P = 0; P < n[a]; ++P) nat[a][P] = P / f2 + f1[a] * (P % f2);
+            if (a == 0) nat[0][h] = h;
+        }
+        std::vector<double> km[3];
+        for (int a = 0; a < 3; ++a) {
+            km[a].resize(nat[a].size());
+            for (size_t P = 0; P < nat[a].size(); ++P) km[a][P] = kmod(nat[a][P], L[a], dx[a], key.p, p->stag);
+        }
+        double* tk = tab.data() + p->tab_k_off[ti];
+        for (int P = 0; P < lxh; ++P) tk[P] = km[0][P];
+        for (int P = 0; P < L[1]; ++P) tk[lxh + P] = km[1][P];
+        for (int P = 0; P < L[2]; ++P) tk[lxh + L[1] + P] = km[2][P];
+        if (p->stag) {
+            cd* ph = tabc.data() + p->tab_ph_off[ti];
+            for (int P = 0; P < lxh; ++P) ph[P] = std::exp(cd(0, -kexact(nat[0][P], L[0], dx[0]) * dx[0] / 2));
+            for (int P = 0; P < L[1]; ++P) ph[lxh + P] = std::exp(cd(0, -kexact(nat[1][P], L[1], dx[1]) * dx[1] / 2));
+            for (int P = 0; P < L[2]; ++P) ph[lxh + L[1] + P] = std::exp(cd(0, -kexact(nat[2][P], L[2], dx[2]) * dx[2] / 2));
+        }
+        // Eq. 1 coefficients per mode, scaled by 1/(Lx Ly Lz) (the inverse
+        // transforms are unnormalised); 1/|k| is not scaled
+        const double invN = 1.0 / (double(L[0]) * L[1] * L[2]);
+        const int64_t NM = int64_t(L[2]) * q;
+        double* tc = tab.data() + p->tab_coef_off[ti];
+        for (int zp = 0; zp < L[2]; ++zp)
+            for (int yp = 0; yp < L[1]; ++yp)
+                for (int xp = 0; xp < lxh; ++xp) {
+                    const double kx = km[0][xp], ky = km[1][yp], kz = km[2][zp];
+                    const double k = std::sqrt(kx * kx + ky * ky + kz * kz);
+                    const double x = k * c_dt;
+                    const double C = std::cos(x), S = std::sin(x);
+                    const double omc = 2.0 * std::sin(x / 2) * std::sin(x / 2);
+                    double Sk, omck, dk, inv;
+                    if (k > 0) {
+                        Sk = S / k; omck = omc / k; inv = 1.0 / k;
+                        dk = (std::fabs(x) < 1e-3) ? c_dt * (-x * x / 6.0 + x * x * x * x / 120.0) : Sk - c_dt;
+                    } else {
+                        Sk = c_dt; omck = 0.0; inv = 0.0; dk = 0.0;
+                    }
+                    const int64_t i = int64_t(zp) * q + int64_t(yp) * lxh + xp;
+                    tc[TAB_C * NM + i] = C * invN;
+                    tc[TAB_S * NM + i] = S * invN;
+                    tc[TAB_SK * NM + i] = Sk * invN;
+                    tc[TAB_OMC * NM + i] = omc * invN;
+                    tc[TAB_OMCK * NM + i] = omck * invN;
+                    tc[TAB_DK * NM + i] = dk * invN;
+                    tc[TAB_INVK * NM + i] = inv;
+                }
+    }
+    cudaError_t e;
+    if (p->f64) {
+        e = cudaMemcpy(p->ws + p->off_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && p->n_tabc)
+            e = cudaMemcpy(p->ws + p->off_tabc, tabc.data(), size_t(p->n_tabc) * sizeof(cd), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> t32(tab.begin(), tab.end());
+        e = cudaMemcpy(p->ws + p->off_tab, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && p->n_tabc) {
+            std::vector<float> c32(size_t(p->n_tabc) * 2);
+            for (int64_t i = 0; i < p->n_tabc; ++i) { c32[2 * i] = float(tabc[i].real()); c32[2 * i + 1] = float(tabc[i].imag()); }
+            e = cudaMemcpy(p->ws + p->off_tabc, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "copy coefficient tables");
+    p->coeffs = true;
+    return PSATD_OK;
+}
+
+static int check_fields(psatd_plan_s* p, const psatd_fields* f, bool need_j) {
+    if (!f) return fail(p, PSATD_E_ARG, "null fields");
+    for (int a = 0; a < 3; ++a) {
+        if (!f->E[a] || !f->B[a]) return fail(p, PSATD_E_ARG, "null E or B arena");
+        if (need_j && !f->J[a]) return fail(p, PSATD_E_ARG, "null J arena");
+        const void* ptrs[3] = {f->E[a], f->B[a], need_j ? f->J[a] : f->E[a]};
+        for (auto q : ptrs) if (reinterpret_cast<uintptr_t>(q) % 16) return fail(p, PSATD_E_ARG, "field arenas must be 16-byte aligned");
+    }
+    if (need_j && p->diag) {
+        if (!f->rho) return fail(p, PSATD_E_ARG, "PSATD_GAUSS_DIAG needs rho");
+        if (reinterpret_cast<uintptr_t>(f->rho) % 16) return fail(p, PSATD_E_ARG, "rho must be 16-byte aligned");
+    }
+    return PSATD_OK;
+}
+
+static LaunchCommon common(psatd_plan_s* p, const psatd_fields* f) {
+    LaunchCommon c;
+    std::memset(&c, 0, sizeof(c));
+    c.subs = p->ws + p->off_desc;
+    c.segs = p->ws + p->off_seg;
+    c.tw = p->ws + p->off_tw;
+    c.tab = p->ws + p->off_tab;
+    c.tabc = p->ws + p->off_tabc;
+    c.spec = p->ws + p->off_spec;
+    for (int a = 0; a < 3; ++a) { c.eb[a] = f->E[a]; c.eb[3 + a] = f->B[a]; c.jr[a] = f->J[a]; }
+    c.jr[3] = f->rho;
+    c.gauss_part = reinterpret_cast<double*>(p->ws + p->off_gauss);
+    c.nsub = int(p->desc.size());
+    c.nseg = int(p->segs.size());
+    c.nf = p->nf;
+    c.staggered = p->stag ? 1 : 0;
+    c.own_only = 0;
+    return c;
+}
+
+static cudaError_t stage(psatd_plan_s* p, int st, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
+    return p->f64 ? launch_stage_f64(st, c, i0, n, smem, s) : launch_stage_f32(st, c, i0, n, smem, s);
+}
+
+int psatd_exchange_guards(psatd_plan_t p, const psatd_fields* f, void* stream) {
+    if (!p) return PSATD_E_ARG;
+    if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
+    int r = check_fields(p, f, false);
+    if (r) return r;
+    LaunchCommon c = common(p, f);
+    cudaError_t e = stage(p, 3, c, 0, p->exch_items, 0, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(p, e, "exchange launch");
+    return PSATD_OK;
+}
+
+int psatd_push(psatd_plan_t p, const psatd_fields* f, double* gauss_dev, void* stream) {
+    if (!p) return PSATD_E_ARG;
+    if (!p->ws || !p->coeffs) return fail(p, PSATD_E_STATE, "workspace and coefficients must be set before psatd_push");
+    int r = check_fields(p, f, true);
+    if (r) return r;
+    if (gauss_dev && !p->diag) return fail(p, PSATD_E_ARG, "gauss output needs PSATD_GAUSS_DIAG");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LaunchCommon c = common(p, f);
+    cudaError_t e = cudaSuccess;
+    if (!p->plain) {
+        if ((e = stage(p, 0, c, 0, p->items[0], p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
+        if ((e = stage(p, 1, c, 0, p->items[1], p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        if ((e = stage(p, 2, c, 0, p->items[2], p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+    } else {
+        c.own_only = 1;
+        const int nsub = int(p->desc.size());
+        for (int i = 0; i < nsub; ++i) {
+            const SubDesc& d = p->desc[i];
+            if ((e = stage(p, 0, c, d.itemA, int64_t(p->nf) * d.L[2], p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
+            if ((e = stage(p, 1, c, d.itemB, (d.q + d.chunkB - 1) / d.chunkB, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+            if ((e = stage(p, 2, c, d.itemC, 6 * int64_t(d.nv[2]), p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+        }
+        if ((e = stage(p, 3, c, 0, p->exch_items, 0, s)) != cudaSuccess) return cuda_fail(p, e, "exchange launch");
+    }
+    if (p->diag && gauss_dev) {
+        e = launch_gauss_reduce(c.subs, c.nsub, c.gauss_part, gauss_dev, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "gauss reduce launch");
+    }
+    return PSATD_OK;
+}
+
+int psatd_destroy(psatd_plan_t p) {
+    delete p;
+    return PSATD_OK;
+}
+
+}  // extern "C"

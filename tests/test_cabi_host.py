@@ -1,0 +1,131 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every symbol declared in include/psatd.h, and plan creation validates the
+decomposition (Sec. 3.2) without touching a device."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1707_08500_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1707_08500_gb300 import build
+    build.build()
+    from paper_1707_08500_gb300 import psatd
+    psatd.lib()
+    return psatd
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "psatd.h")).read()
+    return sorted(set(re.findall(r"\b(psatd_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported(P):
+    names = _declared()
+    assert "psatd_push" in names and "psatd_plan_create" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (psatd_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(P.lib(), n)
+    assert set(P.EXPORTS) == set(names)
+
+
+def test_plan_counts_for_every_workload(P):
+    for name in I.WORKLOADS:
+        wl = I.workload(name)
+        flags = P.PSATD_F64 if wl.precision == "f64" else P.PSATD_F32
+        if wl.staggered:
+            flags |= P.PSATD_STAGGERED
+        h = P.psatd_plan_create(wl.global_n, wl.subs, flags)
+        try:
+            n = P.psatd_arena_elems(h)
+            assert n >= wl.local_cells
+            for s in (0, len(wl.subs) - 1):
+                off, ln = P.psatd_layout(h, s)
+                assert ln == wl.subs[s].local
+                assert off % 64 == 0 and off + ln[0] * ln[1] * ln[2] <= n
+            assert P.psatd_workspace_bytes(h) > 0
+            assert P.psatd_push_launches(h) in (3, 4)
+        finally:
+            P.psatd_destroy(h)
+
+
+def test_plain_schedule_launch_count(P):
+    wl = I.workload("yee64")
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F64 | P.PSATD_STAGGERED | P.PSATD_PLAIN)
+    assert P.psatd_push_launches(h) == 3 * 8 + 1
+    P.psatd_destroy(h)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("overlap", -2), ("gap", -2), ("outside", -2), ("odd_order", -2),
+    ("odd_local_x", -5), ("big_prime", -5), ("no_precision", -1), ("both_precisions", -1),
+])
+def test_plan_rejects_bad_input(P, case, code):
+    g = (32, 32, 32)
+    subs = I.tensor_decomposition([16, 16], [32], [32], 4, 8)
+    flags = P.PSATD_F32
+    if case == "overlap":
+        subs = [subs[0], I.Sub((8, 0, 0), (24, 32, 32), 4, 8)]
+    elif case == "gap":
+        subs = [subs[0]]
+    elif case == "outside":
+        subs = [subs[0], I.Sub((16, 0, 0), (17, 32, 32), 4, 8)]
+    elif case == "odd_order":
+        subs = [I.Sub(s.lo, s.n, s.ng, 7) for s in subs]
+    elif case == "odd_local_x":
+        subs = I.tensor_decomposition([15, 17], [32], [32], 4, 8)
+    elif case == "big_prime":
+        g = (32, 34, 32)
+        subs = I.tensor_decomposition([16, 16], [34], [32], 4, 8)     # 42 = 2*3*7 ok, use 17 below
+        subs = [I.Sub(s.lo, s.n, 0, 8) for s in subs]                 # local y = 34 = 2*17: no split
+    elif case == "no_precision":
+        flags = 0
+    elif case == "both_precisions":
+        flags = P.PSATD_F32 | P.PSATD_F64
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_plan_create(g, subs, flags)
+    assert e.value.code == code
+
+
+def test_status_strings(P):
+    for c in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert P.psatd_status_string(c)
+    assert P.psatd_status_string(-99) == "unknown status"
+
+
+def test_state_errors_without_gpu(P):
+    wl = I.workload("plain32")
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F64)
+    f = P.FieldsT()
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_push(h, f)
+    assert e.value.code == -6            # no workspace yet
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_set_coeffs(h, 0.5, (1.0, 1.0, 1.0))
+    assert e.value.code == -6
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_set_workspace(h, 0x1001, 1 << 30)   # misaligned: rejected before any copy
+    assert e.value.code == -1
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_set_workspace(h, 0x1000, 16)        # too small
+    assert e.value.code == -3
+    P.psatd_destroy(h)
+
+
+def test_exchange_segments_cover_every_local_cell_once(P):
+    """Host bookkeeping of the guard exchange: the plan's arena size and the
+    tiling checks accept guard widths larger than a neighbour's width."""
+    g = (40, 16, 16)
+    subs = I.tensor_decomposition([8, 32], [16], [16], 10, 4)
+    h = P.psatd_plan_create(g, subs, P.PSATD_F32)
+    assert P.psatd_layout(h, 0)[1] == (28, 36, 36)
+    P.psatd_destroy(h)
