@@ -1,0 +1,379 @@
+"""Throughput of the local-FFT PSATD push on one GB300 (arXiv:1707.08500, Sec. 3).
+
+Default workload: the plasma-mirror-shaped grid, 1024x512x512 cells cut into
+16x8x8 subdomains of 64^3 with 16 guards (96^3 local FFTs), order p = 100,
+FP32 batched schedule with the Gauss diagnostic (10 fields in, 6 out).
+
+One step = one psatd_push (passes A, B, C and the Gauss reduction) over all
+1024 subdomains.  Inputs (906 M local cells x 10 fields, 36 GB) are far larger
+than L2, so no flush is needed between steps.  The JSON line also carries the
+per-stage roofline of the dominant kernel, the plain one-subdomain-per-launch
+FP64 GPU path, an end-to-end number through the C ABI with per-step host
+copies, and the FP64 CPU oracle timed on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------
+def stage_bytes(wl, nf: int, esz: int):
+    """Algorithmic HBM bytes per launch of each stage (unique inputs + outputs):
+    A reads nf real fields and writes nf half spectra; B reads nf spectra and
+    writes 6 spectra on the valid z planes; C reads those and writes 6 real
+    fields on every local cell (own box plus guard images)."""
+    A = B = C = 0
+    local = 0
+    for sd in wl.subs:
+        lx, ly, lz = sd.local
+        cells = lx * ly * lz
+        spec = lz * ly * (lx // 2 + 1) * 2 * esz
+        vspec = sd.n[2] * ly * (lx // 2 + 1) * 2 * esz
+        A += nf * (cells * esz + spec)
+        B += nf * spec + 6 * vspec
+        C += 6 * (vspec + cells * esz)
+        local += cells
+    return {"A": A, "B": B, "C": C}, local
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_mirror1024.json")) as f:
+            t = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1707_08500_gb300", "csrc", "psatd_kernels.cu"), "rb").read()
+        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return t["bytes_per_launch"].get(kernel)
+    except Exception:
+        return None
+
+
+def fill_solver(sol, wl, device):
+    """Write every subdomain's padded box of all ten fields (FP64 synthesis on
+    the device, cast to the solver's precision)."""
+    from paper_1707_08500_gb300 import inputs as I
+    import torch
+    if wl.fields == "laser_slab":
+        for s, sd in enumerate(wl.subs):
+            b = I.box_fields(wl, sd, device=device)
+            for n in I.FIELD_NAMES:
+                sol.box(n, s).copy_(b[n])
+            del b
+    else:
+        glob = I.global_fields(wl)
+        sol.load_global(glob)
+    torch.cuda.synchronize()
+
+
+def cpu_oracle_sample(wl, budget_s: float):
+    """FP64 oracle (as it stands) on whole subdomain steps until the budget is spent."""
+    from oracle import psatd_oracle as O
+    from paper_1707_08500_gb300 import inputs as I
+    t_used, cells, nsub = 0.0, 0, 0
+    for sd in wl.subs[:: max(1, len(wl.subs) // 64)]:
+        b = {k: v.numpy() for k, v in I.box_fields(wl, sd, device="cpu").items()}
+        t0 = time.perf_counter()
+        O.local_push(b, sd.local, wl.dx, sd.p, wl.c_dt, wl.staggered)
+        t_used += time.perf_counter() - t0
+        cells += sd.n[0] * sd.n[1] * sd.n[2]
+        nsub += 1
+        if t_used > budget_s:
+            break
+    return {"value": cells / t_used / 1e9, "unit": "Gcell-steps/s", "cores": O.WORKERS, "kind": "oracle",
+            "sample": f"{nsub} of {len(wl.subs)} subdomain steps ({cells} valid cells), {t_used:.1f} s"}
+
+
+# ------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1707_08500_gb300 import build as B
+    from paper_1707_08500_gb300 import inputs as I
+    from paper_1707_08500_gb300 import psatd as P
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = I.workload(args.workload)
+    gauss = not args.no_gauss
+    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev)
+    fill_solver(sol, wl, dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def mkev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    for _ in range(args.warmup):
+        sol.push(sp)
+    torch.cuda.synchronize()
+    evs = [[mkev() for _ in range(4)] for _ in range(args.steps)]
+    t0, t1 = mkev(), mkev()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(args.steps):
+            P.psatd_push_profiled(sol.plan, sol.fields, sol.gauss_out.data_ptr() if gauss else None, sp,
+                                  [e.cuda_event for e in evs[k]])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = t0.elapsed_time(t1)
+    stage_ms = {st: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
+                for i, st in enumerate("ABC")}
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    valid = wl.valid_cells
+    value = valid * world / (ms_step / 1e3) / 1e9
+    nf = 10 if gauss else 9
+    by, local = stage_bytes(wl, nf, 4)
+    peak, peak_kind = _peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    names = {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"}
+    stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
+                   "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
+    achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
+    fused_bytes = (64 if gauss else 60) * local
+    result = {
+        "metric": "Gcell-steps/s of local-FFT PSATD push (valid cells x steps / s), batched FP32; % HBM roof",
+        "value": round(value, 4), "unit": "Gcell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "global_n": list(wl.global_n), "subdomains": len(wl.subs),
+                   "local_n": list(wl.subs[0].local), "guards": wl.subs[0].ng, "order": wl.subs[0].p,
+                   "c_dt": wl.c_dt, "gauss_diag": gauss, "valid_cells": valid, "local_cells": local,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs (36 GB) larger than L2; no flush"},
+        "local_gcell_steps": round(local * world / (ms_step / 1e3) / 1e9, 4),
+        "stages": stages,
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(names[dom]),
+                     "peak_kind": peak_kind},
+        "step_roofline": {"alg_bytes_per_step_fused": fused_bytes,
+                          "frac_of_fused_floor": round(fused_bytes / (ms_step / 1e3) / 1e9 / peak, 4),
+                          "three_pass_bytes_per_step": sum(by.values()),
+                          "frac_three_pass": round(sum(by.values()) / (ms_step / 1e3) / 1e9 / peak, 4)},
+        "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
+        "clocks": clk.summary(),
+    }
+    # ---- end to end through the C ABI with per-step host copies ----------------
+    if not args.skip_e2e:
+        names_in = ("Jx", "Jy", "Jz", "rho") if gauss else ("Jx", "Jy", "Jz")
+        host = {n: torch.empty(sol.arena_elems, dtype=torch.float32, pin_memory=True) for n in names_in}
+        for n in names_in:
+            host[n].copy_(sol.arenas[n])
+        gh = torch.empty(2 * len(wl.subs), dtype=torch.float64, pin_memory=True)
+        ksteps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0, e1 = mkev(), mkev()
+        e0.record(stream)
+        for _ in range(ksteps):
+            for n in names_in:
+                sol.arenas[n].copy_(host[n], non_blocking=True)
+            sol.push(sp)
+            if gauss:
+                gh.copy_(sol.gauss_out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / ksteps
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        result["e2e"] = {"value": round(valid * world / (ems / 1e3) / 1e9, 4), "unit": "Gcell-steps/s",
+                         "h2d_bytes_per_step": sum(h.numel() * 4 for h in host.values()),
+                         "d2h_bytes_per_step": gh.numel() * 8 if gauss else 0, "steps": ksteps,
+                         "ms_per_step": round(ems, 3),
+                         "what": "per step: J (and rho) copied from pinned host, psatd_push, Gauss sums read back"}
+        del host
+    # ---- plain FP64 GPU path and FP32-vs-FP64 agreement ------------------------
+    if not args.skip_plain and rank == 0:
+        del sol
+        torch.cuda.empty_cache()
+        s64 = P.Solver(wl, precision="f64", plain=True, gauss=gauss, device=dev)
+        fill_solver(s64, wl, dev)
+        s64.push(sp)
+        torch.cuda.synchronize()
+        nst = 2
+        e0, e1 = mkev(), mkev()
+        e0.record(stream)
+        for _ in range(nst):
+            s64.push(sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / nst
+        s32 = P.Solver(wl, precision="f32", gauss=gauss, device=dev)
+        fill_solver(s32, wl, dev)
+        for _ in range(1 + nst):
+            s32.push(sp)
+        torch.cuda.synchronize()
+        num = den = 0.0
+        for n in I.EB_NAMES:
+            d = (s32.arenas[n].double() - s64.arenas[n])
+            num += float((d * d).sum())
+            den += float((s64.arenas[n] * s64.arenas[n]).sum())
+        pv = valid / (pms / 1e3) / 1e9
+        result["plain_f64"] = {"value": round(pv, 5), "unit": "Gcell-steps/s", "ms_per_step": round(pms, 2),
+                               "speedup_of_batched_f32": round(value / world / pv, 2),
+                               "f32_vs_f64_rel_l2_after_3_steps": float(f"{math.sqrt(num / den):.3e}"),
+                               "launches_per_step": P.psatd_push_launches(s64.plan)}
+        del s64, s32
+        torch.cuda.empty_cache()
+    # ---- CPU oracle baseline (rank 0, N = 1 only) -------------------------------
+    if not args.skip_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_budget)
+    return result
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle, timed as it stands on the host cores."""
+    from oracle import psatd_oracle as O
+    from paper_1707_08500_gb300 import inputs as I
+    if rank != 0:
+        return None
+    wl = I.workload(args.workload)
+    per_step = max(1, int(args.ref_subs))
+    boxes = [(sd, {k: v.numpy() for k, v in I.box_fields(wl, sd, device="cpu").items()})
+             for sd in wl.subs[:per_step]]
+
+    def one():
+        for sd, b in boxes:
+            O.local_push(b, sd.local, wl.dx, sd.p, wl.c_dt, wl.staggered)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    cells = sum(sd.n[0] * sd.n[1] * sd.n[2] for sd, _ in boxes)
+    v = cells / dt / 1e9
+    sample = f"each step = {len(boxes)} of {len(wl.subs)} subdomain pushes ({cells} valid cells)"
+    return {"impl": "reference", "metric": "Gcell-steps/s of local-FFT PSATD push (valid cells x steps / s), batched FP32; % HBM roof",
+            "value": round(v, 6), "unit": "Gcell-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "global_n": list(wl.global_n), "subdomains": len(wl.subs)},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gcell-steps/s", "cores": O.WORKERS,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mirror1024")
+    ap.add_argument("--no-gauss", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-subs", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -131,6 +131,15 @@ int psatd_set_coeffs(psatd_plan_t plan, double c_dt, const double dx[3]);
  * PSATD_GAUSS_DIAG. */
 int psatd_push(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev, void* stream);
 
+/* psatd_push that also records caller-created CUDA events on `stream` at the
+ * stage boundaries of the batched schedule: events[0] before pass A (forward
+ * x/y), events[1] after pass A, events[2] after pass B (z transforms and
+ * Eq. 1), events[3] after pass C (inverse y/x and guard images).  Any entry
+ * may be NULL.  With PSATD_PLAIN only events[0] and events[3] are recorded.
+ * Used to time each stage inside a running loop. */
+int psatd_push_profiled(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev, void* stream,
+                        void* const events[4]);
+
 /* Copy every valid cell into each guard cell that images it (all 26
  * neighbour directions, periodic wrap), for E and B only, on `stream`. */
 int psatd_exchange_guards(psatd_plan_t plan, const psatd_fields* fields, void* stream);

@@ -34,7 +34,9 @@ struct SubDesc {
     int64_t tab_ph;      // complex offset of stagger phases (same layout), or -1
     int seg_begin, seg_end;     // exchange segments whose source is this subdomain
     int64_t itemA, itemB, itemC; // first work item of this subdomain in each stage
-    int chunkB;          // modes per pass-B chunk (M)
+    int chunkB;          // modes per pass-B chunk (M, a power of two)
+    int lgB;             // log2(M)
+    int fsB;             // padded stride between fields of a pass-B chunk in shared memory
     int pad1;
 };
 
@@ -48,6 +50,7 @@ struct Segment {
     int ex, ey, ez;      // extents
     int dx, dy, dz;      // destination local = source local + (dx, dy, dz)
     int identity;        // 1 when it is the source's own valid box (dst == src, no shift)
+    int vec4;            // 1 when rows can be stored as aligned 4-element vectors
     int64_t item;        // first exchange work item (one per z row of the segment)
 };
 

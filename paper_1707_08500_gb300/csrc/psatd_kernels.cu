@@ -28,11 +28,38 @@
 
 namespace psatd {
 
+// A table twiddle as an FP32 hi + lo pair (lo = 0 in FP64).
+template <typename T>
+struct alignas(4 * sizeof(T)) twd { cpx<T> hi, lo; };
+
+template <typename T>
+__device__ __forceinline__ twd<T> ld_tw(const twd<T>* p) {
+    twd<T> t;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        t.hi = mk(v.x, v.y);
+        t.lo = mk(v.z, v.w);
+    } else {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        t.hi = mk(v.x, v.y);
+        t.lo = mk(0.0, 0.0);
+    }
+    return t;
+}
+template <typename T>   // v * w
+__device__ __forceinline__ cpx<T> mul_tw(cpx<T> v, const twd<T>& w) {
+    return cmul_const(v, w.hi.x, w.lo.x, w.hi.y, w.lo.y);
+}
+template <typename T>   // v * conj(w)
+__device__ __forceinline__ cpx<T> mul_tw_conj(cpx<T> v, const twd<T>& w) {
+    return cmul_const(v, w.hi.x, w.lo.x, -w.hi.y, -w.lo.y);
+}
+
 template <typename T>
 struct Args {
     const SubDesc* subs;
     const Segment* segs;
-    const cpx<T>* tw;       // twiddle pool
+    const twd<T>* tw;       // twiddle pool (hi/lo pairs)
     const T* tab;           // real tables (coefficients, wavenumbers)
     const cpx<T>* tabc;     // complex tables (stagger phases)
     cpx<T>* spec;           // spectra
@@ -61,84 +88,131 @@ __device__ __forceinline__ cpx<T> ldcs_c(const cpx<T>* p) {
     return mk(v.x, v.y);
 }
 
+template <typename T>
+struct cpx4 { T a, b, c, d; };
+template <typename T> struct vec4;
+template <> struct vec4<float> { using type = float4; };
+template <> struct vec4<double> { using type = double4; };
+template <typename T>   // streaming load of 4 consecutive reals (16-byte aligned for float)
+__device__ __forceinline__ cpx4<T> ldcs4(const T* p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+        return cpx4<T>{v.x, v.y, v.z, v.w};
+    } else {
+        const double2 u = __ldcs(reinterpret_cast<const double2*>(p));
+        const double2 w = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+        return cpx4<T>{u.x, u.y, w.x, w.y};
+    }
+}
+template <typename T>
+__device__ __forceinline__ void stcs4(T* p, cpx4<T> v) {
+    if constexpr (sizeof(T) == 4) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v.a, v.b, v.c, v.d));
+    } else {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v.a, v.b));
+        __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v.c, v.d));
+    }
+}
+template <typename T>
+__device__ __forceinline__ void stcs_c(cpx<T>* p, cpx<T> v) {
+    using V = typename vec2<T>::type;
+    V w; w.x = v.x; w.y = v.y;
+    __stcs(reinterpret_cast<V*>(p), w);
+}
+
+// Batched transforms in shared memory.  Transform b starts at b*s_in
+// (single-level) or (b mod 2^lg)*s_in + (b >> lg)*s_out (two-level, used for
+// several fields of one pencil chunk); its elements are es apart.
 struct Batch {
     int count;   // number of transforms
-    int inner;   // transforms per outer group
-    int s_in;    // stride between transforms of a group
-    int s_out;   // stride between groups
-    int es;      // stride between elements of one transform
+    int s_in;
+    int lg;      // log2 of transforms per group (two-level batches only)
+    int s_out;
+    int es;
 };
 
+template <bool TWO>
 __device__ __forceinline__ int boff(const Batch& b, int i) {
-    const int o = i / b.inner;
-    return (i - o * b.inner) * b.s_in + o * b.s_out;
+    if constexpr (TWO) return (i & ((1 << b.lg) - 1)) * b.s_in + (i >> b.lg) * b.s_out;
+    else return i * b.s_in;
+}
+
+// Visit every (outer, inner) pair with inner in [0, count), outer in
+// [0, nouter), pair index outer*count + inner = threadIdx.x + k*kThreads,
+// without a division per pair (the inner step is always < count).
+template <class F>
+__device__ __forceinline__ void loop2(int count, int nouter, F&& f) {
+    int o = int(threadIdx.x) / count;
+    int i = int(threadIdx.x) - o * count;
+    const int dO = kThreads / count, dI = kThreads - dO * count;
+    while (o < nouter) {
+        f(o, i);
+        i += dI;
+        o += dO;
+        if (i >= count) { i -= count; ++o; }
+    }
 }
 
 // ---- shared-memory FFT stages ---------------------------------------------
-// Strided stage: each item loads R values at positions j + r*stride, does an
-// R-point DFT and (forward only) multiplies output r by w^{j r}; stores in place.
-template <int R, bool INV, bool TW, typename T>
+// Strided stage: item (j, b) loads the R values at positions j + r*stride of
+// transform b, does an R-point DFT and (forward only) multiplies output r by
+// w^{j r}; stores in place.
+template <int R, bool INV, bool TW, bool TWO, typename T>
 __device__ __forceinline__ void stage_strided(cpx<T>* sm, const Batch& bt, int stride,
-                                              const cpx<T>* __restrict__ tw) {
-    const int items = bt.count * stride;
+                                              const twd<T>* __restrict__ tw) {
     const int es = bt.es * stride;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-        const int j = it / bt.count;
-        const int b = it - j * bt.count;
-        cpx<T>* p = sm + boff(bt, b) + j * bt.es;
+    loop2(bt.count, stride, [&](int j, int b) {
+        cpx<T>* p = sm + boff<TWO>(bt, b) + j * bt.es;
         cpx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = p[r * es];
         Dft<R, INV>::run(v);
         if constexpr (TW) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], ldg_c(tw + j * r));
+            for (int r = 1; r < R; ++r) v[r] = mul_tw(v[r], ld_tw(tw + j * r));
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) p[r * es] = v[r];
-    }
+    });
 }
 
-// Block stage: each item k loads the R contiguous values k*R + r, does an
-// R-point DFT and (inverse only) multiplies output r by conj(w^{r k}).
-template <int R, bool INV, bool TW, typename T>
+// Block stage: item (k, b) loads the R contiguous values k*R + r of transform
+// b, does an R-point DFT and (inverse only) multiplies output r by conj(w^{r k}).
+template <int R, bool INV, bool TW, bool TWO, typename T>
 __device__ __forceinline__ void stage_block(cpx<T>* sm, const Batch& bt, int nblk,
-                                            const cpx<T>* __restrict__ tw) {
-    const int items = bt.count * nblk;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-        const int k = it / bt.count;
-        const int b = it - k * bt.count;
-        cpx<T>* p = sm + boff(bt, b) + k * R * bt.es;
+                                            const twd<T>* __restrict__ tw) {
+    loop2(bt.count, nblk, [&](int k, int b) {
+        cpx<T>* p = sm + boff<TWO>(bt, b) + k * R * bt.es;
         cpx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = p[r * bt.es];
         Dft<R, INV>::run(v);
         if constexpr (TW) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], ldg_c(tw + r * k));
+            for (int r = 1; r < R; ++r) v[r] = mul_tw_conj(v[r], ld_tw(tw + r * k));
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) p[r * bt.es] = v[r];
-    }
+    });
 }
 
 // natural order in -> position order out
-template <typename T>
-__device__ __forceinline__ void fft_fwd(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const cpx<T>* tw) {
-    const cpx<T>* w = tw + ax.tw;
-    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, false, true>(sm, bt, ax.f2, w); });
+template <bool TWO, typename T>
+__device__ __forceinline__ void fft_fwd(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const twd<T>* tw) {
+    const twd<T>* w = tw + ax.tw;
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, false, true, TWO>(sm, bt, ax.f2, w); });
     __syncthreads();
-    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, false, false>(sm, bt, ax.f1, w); });
+    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, false, false, TWO>(sm, bt, ax.f1, w); });
     __syncthreads();
 }
 
 // position order in -> natural order out (unnormalised)
-template <typename T>
-__device__ __forceinline__ void fft_inv(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const cpx<T>* tw) {
-    const cpx<T>* w = tw + ax.tw;
-    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, true, true>(sm, bt, ax.f1, w); });
+template <bool TWO, typename T>
+__device__ __forceinline__ void fft_inv(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const twd<T>* tw) {
+    const twd<T>* w = tw + ax.tw;
+    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, true, true, TWO>(sm, bt, ax.f1, w); });
     __syncthreads();
-    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, true, false>(sm, bt, ax.f2, w); });
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, true, false, TWO>(sm, bt, ax.f2, w); });
     __syncthreads();
 }
 
@@ -166,7 +240,7 @@ __device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
 
 // ---- pass A: x (real) and y forward transforms of one plane ---------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pass_a(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
@@ -175,19 +249,27 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Args<T> a) {
         const int loc = int(it - d.itemA);
         const int f = loc / Lz, z = loc - (loc / Lz) * Lz;
         const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
-        const cpx<T>* src = reinterpret_cast<const cpx<T>*>(field_in(a, f) + d.field_off + int64_t(z) * Ly * Lx);
-        for (int i = threadIdx.x; i < Ly * h; i += kThreads) {
-            const int y = i / h;
-            sm[y * pitch + (i - y * h)] = ldcs_c(src + i);
+        const T* src = field_in(a, f) + d.field_off + int64_t(z) * Ly * Lx;
+        // packed complex z[m] = x[2m] + i x[2m+1], row y at y*pitch
+        if ((h & 1) == 0) {
+            const int h2 = h >> 1;
+            loop2(h2, Ly, [&](int y, int m) {
+                const cpx4<T> v = ldcs4(src + 4 * (y * h2 + m));
+                cpx<T>* p = sm + y * pitch + 2 * m;
+                p[0] = mk(v.a, v.b);
+                p[1] = mk(v.c, v.d);
+            });
+        } else {
+            loop2(h, Ly, [&](int y, int m) {
+                sm[y * pitch + m] = ldcs_c(reinterpret_cast<const cpx<T>*>(src) + y * h + m);
+            });
         }
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
-        fft_fwd(sm, d.ax, Batch{Ly, Ly, pitch, 0, 1}, a.tw);
+        fft_fwd<false>(sm, d.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
         // split the packed transform into the half spectrum X[0..h]
-        const cpx<T>* wp = a.tw + d.tw_post;
-        const int npair = h / 2 + 1;
-        for (int i = threadIdx.x; i < Ly * npair; i += kThreads) {
-            const int k = i / Ly, y = i - k * Ly;
+        const twd<T>* wp = a.tw + d.tw_post;
+        loop2(Ly, h / 2 + 1, [&](int k, int y) {
             cpx<T>* p = sm + y * pitch;
             if (k == 0) {
                 const cpx<T> z0 = p[0];
@@ -199,25 +281,21 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Args<T> a) {
                 const cpx<T> e = scale(A + Bc, T(0.5));
                 const cpx<T> dd = A - Bc;
                 const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);   // (A - conj B)/(2i)
-                const cpx<T> wo = cmul(ldg_c(wp + k), o);
+                const cpx<T> wo = mul_tw(o, ld_tw(wp + k));
                 p[pa] = e + wo;
                 if (pb != pa) p[pb] = conj(e - wo);
             }
-        }
+        });
         __syncthreads();
         // y: complex FFT of length Ly over the lxh columns
-        fft_fwd(sm, d.ay, Batch{lxh, lxh, 1, 0, pitch}, a.tw);
+        fft_fwd<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
         cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
-        for (int i = threadIdx.x; i < d.q; i += kThreads) {
-            const int y = i / lxh;
-            dst[i] = sm[y * pitch + (i - y * lxh)];
-        }
+        loop2(lxh, Ly, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
         __syncthreads();
     }
 }
 
 // ---- pass B: z transforms and the Eq. 1 update -----------------------------
-template <typename T>
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -233,34 +311,35 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pass_b(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ double red[2][kThreads / 32];
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
         const SubDesc& d = a.subs[find_sub<1>(a.subs, a.nsub, it)];
         const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
-        const int M = d.chunkB, Q = d.q, lxh = d.lxh;
+        const int M = d.chunkB, lgM = d.lgB, Q = d.q, lxh = d.lxh;
         const int q0 = int(it - d.itemB) * M;
         const int mc = min(M, Q - q0);
         const int nf = a.nf;
-        const int fs = Lz * M;                         // field stride in shared memory
+        const int fs = d.fsB;                          // padded field stride in shared memory
         cpx<T>* spec = a.spec + d.spec_off;
-        for (int i = threadIdx.x; i < nf * fs; i += kThreads) {
-            const int r = i / M, m = i - r * M;
-            const int f = r / Lz, z = r - f * Lz;
-            sm[i] = m < mc ? ldcs_c(spec + int64_t(f * Lz + z) * Q + q0 + m) : mk(T(0), T(0));
+        for (int f = 0; f < nf; ++f) {
+            const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
+            cpx<T>* s = sm + f * fs;
+            loop2(M, Lz, [&](int z, int m) {
+                s[z * M + m] = m < mc ? ldcs_c(src + int64_t(z) * Q + m) : mk(T(0), T(0));
+            });
         }
         __syncthreads();
-        fft_fwd(sm, d.az, Batch{nf * M, M, 1, fs, M}, a.tw);
+        fft_fwd<true>(sm, d.az, Batch{nf * M, 1, lgM, fs, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
         const T* __restrict__ tk = a.tab + d.tab_k;
         const T Nfull = T(double(Lx) * double(Ly) * double(Lz));
         double g_res = 0.0, g_rho = 0.0;
-        for (int i = threadIdx.x; i < fs; i += kThreads) {
-            const int zp = i / M, m = i - (i / M) * M;
-            if (m >= mc) continue;
+        loop2(M, Lz, [&](int zp, int m) {
+            if (m >= mc) return;
             const int q = q0 + m;
             const int yp = q / lxh, xp = q - yp * lxh;
             const T* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q;
@@ -268,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Args<T> a) {
             const T omCk = __ldg(tb + 4 * NM), Dk = __ldg(tb + 5 * NM), inv = __ldg(tb + 6 * NM);
             const T kx = __ldg(tk + xp), ky = __ldg(tk + lxh + yp), kz = __ldg(tk + lxh + Ly + zp);
             const T hx = kx * inv, hy = ky * inv, hz = kz * inv;
-            cpx<T>* p = sm + i;
+            cpx<T>* p = sm + zp * M + m;
             cpx<T> E0 = p[0], E1 = p[fs], E2 = p[2 * fs];
             cpx<T> B0 = p[3 * fs], B1 = p[4 * fs], B2 = p[5 * fs];
             cpx<T> J0 = p[6 * fs], J1 = p[7 * fs], J2 = p[8 * fs];
@@ -313,21 +392,20 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Args<T> a) {
             }
             p[0] = F0; p[fs] = F1; p[2 * fs] = F2;
             p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
-        }
+        });
         __syncthreads();
-        fft_inv(sm, d.az, Batch{6 * M, M, 1, fs, M}, a.tw);
+        fft_inv<true>(sm, d.az, Batch{6 * M, 1, lgM, fs, M}, a.tw);
         const int ng = d.ng, nz = d.nv[2];
-        for (int i = threadIdx.x; i < 6 * nz * M; i += kThreads) {
-            const int r = i / M, m = i - r * M;
-            const int f = r / nz, zv = r - f * nz;
-            if (m < mc) {
-                const int z = ng + zv;
-                spec[int64_t(f * Lz + z) * Q + q0 + m] = sm[f * fs + z * M + m];
-            }
+        for (int f = 0; f < 6; ++f) {
+            cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng) * Q + q0;
+            const cpx<T>* s = sm + f * fs + ng * M;
+            loop2(M, nz, [&](int zv, int m) {
+                if (m < mc) stcs_c(dst + int64_t(zv) * Q + m, s[zv * M + m]);
+            });
         }
         if (nf > 9) {
-            const double s1 = block_sum<T>(g_res, red[0]);
-            const double s2 = block_sum<T>(g_rho, red[1]);
+            const double s1 = block_sum(g_res, red[0]);
+            const double s2 = block_sum(g_rho, red[1]);
             if (threadIdx.x == 0) {
                 a.gauss_part[2 * it] = s1;
                 a.gauss_part[2 * it + 1] = s2;
@@ -339,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Args<T> a) {
 
 // ---- pass C: inverse y and x transforms, fused guard replacement ------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pass_c(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
@@ -351,18 +429,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(Args<T> a) {
         const int f = loc / nz, z = ng + (loc - (loc / nz) * nz);
         const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
         const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
-        for (int i = threadIdx.x; i < d.q; i += kThreads) {
-            const int y = i / lxh;
-            sm[y * pitch + (i - y * lxh)] = ldcs_c(src + i);
-        }
+        loop2(lxh, Ly, [&](int y, int c) { sm[y * pitch + c] = ldcs_c(src + y * lxh + c); });
         __syncthreads();
-        fft_inv(sm, d.ay, Batch{lxh, lxh, 1, 0, pitch}, a.tw);
+        fft_inv<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
-        const cpx<T>* wp = a.tw + d.tw_post;
-        const int npair = h / 2 + 1;
+        const twd<T>* wp = a.tw + d.tw_post;
         cpx<T>* rows = sm + ng * pitch;
-        for (int i = threadIdx.x; i < ny * npair; i += kThreads) {
-            const int k = i / ny, y = i - k * ny;
+        loop2(ny, h / 2 + 1, [&](int k, int y) {
             cpx<T>* p = rows + y * pitch;
             if (k == 0) {
                 const T x0 = p[0].x, xh = p[h].x;        // real parts only (C2R)
@@ -371,26 +444,31 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(Args<T> a) {
                 const int pa = xpos(k, d.ax), pb = xpos(h - k, d.ax);
                 const cpx<T> A = p[pa], Bc = conj(p[pb]);
                 const cpx<T> e = A + Bc;
-                const cpx<T> o = cmulc(A - Bc, ldg_c(wp + k));
+                const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + k));
                 p[pa] = e + mul_i(o);
                 if (pb != pa) p[pb] = conj(e) + mul_i(conj(o));
             }
-        }
+        });
         __syncthreads();
-        fft_inv(rows, d.ax, Batch{ny, ny, pitch, 0, 1}, a.tw);
+        fft_inv<false>(rows, d.ax, Batch{ny, pitch, 0, 0, 1}, a.tw);
         // store the valid cells of this plane to every box that holds them
         T* out = a.eb[f];
         const T* rp = reinterpret_cast<const T*>(sm);
+        const int rs = 2 * pitch;                         // real row stride
         for (int g = d.seg_begin; g < d.seg_end; ++g) {
             const Segment& sg = a.segs[g];
             if (a.own_only && !sg.identity) continue;
             if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
-            T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.dy) * sg.dLx + sg.dx;
-            const int cnt = sg.ex * sg.ey;
-            for (int i = threadIdx.x; i < cnt; i += kThreads) {
-                const int yy = i / sg.ex;
-                const int y = sg.y0 + yy, x = sg.x0 + (i - yy * sg.ex);
-                __stcs(dst + int64_t(y) * sg.dLx + x, rp[y * 2 * pitch + x]);
+            T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
+            const T* sp = rp + sg.y0 * rs + sg.x0;
+            if (sg.vec4) {
+                loop2(sg.ex >> 2, sg.ey, [&](int yy, int x4) {
+                    const cpx<T> u = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4);
+                    const cpx<T> w = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4 + 2);
+                    stcs4(dst + int64_t(yy) * sg.dLx + 4 * x4, cpx4<T>{u.x, u.y, w.x, w.y});
+                });
+            } else {
+                loop2(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
             }
         }
         __syncthreads();
@@ -409,15 +487,11 @@ __global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
         const Segment& sg = a.segs[lo];
         const SubDesc& sd = a.subs[sg.src];
         const int z = sg.z0 + int(it - sg.item);
-        const int cnt = sg.ex * sg.ey;
         for (int f = 0; f < 6; ++f) {
             T* fld = a.eb[f];
             const T* src = fld + sd.field_off + (int64_t(z) * sd.L[1] + sg.y0) * sd.L[0] + sg.x0;
             T* dst = fld + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
-            for (int i = threadIdx.x; i < cnt; i += kThreads) {
-                const int yy = i / sg.ex, xx = i - yy * sg.ex;
-                dst[int64_t(yy) * sg.dLx + xx] = src[int64_t(yy) * sd.L[0] + xx];
-            }
+            loop2(sg.ex, sg.ey, [&](int yy, int xx) { dst[int64_t(yy) * sg.dLx + xx] = src[int64_t(yy) * sd.L[0] + xx]; });
         }
     }
 }
@@ -447,7 +521,7 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     Args<T> a;
     a.subs = static_cast<const SubDesc*>(c.subs);
     a.segs = static_cast<const Segment*>(c.segs);
-    a.tw = static_cast<const cpx<T>*>(c.tw);
+    a.tw = static_cast<const twd<T>*>(c.tw);
     a.tab = static_cast<const T*>(c.tab);
     a.tabc = static_cast<const cpx<T>*>(c.tabc);
     a.spec = static_cast<cpx<T>*>(c.spec);
@@ -468,7 +542,9 @@ static unsigned grid_for(int64_t n) { return unsigned(n < 2147483647 ? n : 21474
 
 template <typename T>
 static cudaError_t set_smem_attr(const void* fn, int bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 template <typename T>

@@ -298,11 +298,18 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
         int M = p->f64 ? 4 : 8;
-        while (M > 1 && int64_t(p->nf) * d.L[2] * M * csz > 100 * 1024) M /= 2;
+        while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 100 * 1024) M /= 2;
         d.chunkB = M;
+        d.lgB = 0;
+        while ((1 << d.lgB) < M) ++d.lgB;
+        // field stride padded so that consecutive fields of a chunk fall on
+        // different shared-memory banks
+        int fs = d.L[2] * M;
+        while ((fs * csz) % 128 != (M * csz) % 128) ++fs;
+        d.fsB = fs;
         p->smemA = std::max(p->smemA, d.L[1] * d.pitch * csz);
         p->smemC = p->smemA;
-        p->smemB = std::max(p->smemB, p->nf * d.L[2] * M * csz);
+        p->smemB = std::max(p->smemB, p->nf * d.fsB * csz);
         d.itemA = iA; iA += int64_t(p->nf) * d.L[2];
         d.itemB = iB; iB += (d.q + M - 1) / M;
         d.itemC = iC; iC += 6 * int64_t(d.nv[2]);
@@ -356,6 +363,7 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
                 g.ex = ext[0]; g.ey = ext[1]; g.ez = ext[2];
                 g.dx = off[0]; g.dy = off[1]; g.dz = off[2];
                 g.identity = (dd == s && t[0] == 0 && t[1] == 0 && t[2] == 0) ? 1 : 0;
+                g.vec4 = (g.x0 % 4 == 0 && (g.x0 + g.dx) % 4 == 0 && g.ex % 4 == 0 && g.dLx % 4 == 0) ? 1 : 0;
                 p->segs.push_back(g);
             }
         }
@@ -371,7 +379,7 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
     size_t o = 0;
     p->off_desc = o; o = align_up(o + sizeof(SubDesc) * p->desc.size(), 256);
     p->off_seg = o; o = align_up(o + sizeof(Segment) * p->segs.size(), 256);
-    p->off_tw = o; o = align_up(o + size_t(p->n_tw) * 2 * esz, 256);
+    p->off_tw = o; o = align_up(o + size_t(p->n_tw) * 4 * esz, 256);   // hi/lo pairs
     p->off_tab = o; o = align_up(o + size_t(p->n_tab) * esz, 256);
     p->off_tabc = o; o = align_up(o + size_t(std::max<int64_t>(p->n_tabc, 1)) * 2 * esz, 256);
     p->off_gauss = o; o = align_up(o + size_t(std::max<int64_t>(p->items[1], 1)) * 2 * sizeof(double), 256);
@@ -428,11 +436,21 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
         for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
     for (auto& kv : p->post_off)
         for (int k = 0; k <= kv.first / 2; ++k) tw[kv.second + k] = unit_root(k, kv.first);
+    // each twiddle is stored as (hi, lo): in FP32 lo is the rounding of the
+    // remainder so that hi + lo carries the FP64 value; in FP64 lo = 0
     if (p->f64) {
-        e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size() * sizeof(cd), cudaMemcpyHostToDevice);
+        std::vector<double> t64(tw.size() * 4, 0.0);
+        for (size_t i = 0; i < tw.size(); ++i) { t64[4 * i] = tw[i].real(); t64[4 * i + 1] = tw[i].imag(); }
+        e = cudaMemcpy(p->ws + p->off_tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
     } else {
-        std::vector<float> t32(tw.size() * 2);
-        for (size_t i = 0; i < tw.size(); ++i) { t32[2 * i] = float(tw[i].real()); t32[2 * i + 1] = float(tw[i].imag()); }
+        std::vector<float> t32(tw.size() * 4);
+        for (size_t i = 0; i < tw.size(); ++i) {
+            const float hr = float(tw[i].real()), hi = float(tw[i].imag());
+            t32[4 * i] = hr;
+            t32[4 * i + 1] = hi;
+            t32[4 * i + 2] = float(tw[i].real() - double(hr));
+            t32[4 * i + 3] = float(tw[i].imag() - double(hi));
+        }
         e = cudaMemcpy(p->ws + p->off_tw, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
@@ -575,18 +593,25 @@ int psatd_exchange_guards(psatd_plan_t p, const psatd_fields* f, void* stream) {
     return PSATD_OK;
 }
 
-int psatd_push(psatd_plan_t p, const psatd_fields* f, double* gauss_dev, void* stream) {
+static int push_impl(psatd_plan_s* p, const psatd_fields* f, double* gauss_dev, void* stream, void* const* ev) {
     if (!p) return PSATD_E_ARG;
     if (!p->ws || !p->coeffs) return fail(p, PSATD_E_STATE, "workspace and coefficients must be set before psatd_push");
     int r = check_fields(p, f, true);
     if (r) return r;
     if (gauss_dev && !p->diag) return fail(p, PSATD_E_ARG, "gauss output needs PSATD_GAUSS_DIAG");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto mark = [&](int i) -> cudaError_t {
+        if (!ev || !ev[i]) return cudaSuccess;
+        return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), s);
+    };
     LaunchCommon c = common(p, f);
     cudaError_t e = cudaSuccess;
+    if ((e = mark(0)) != cudaSuccess) return cuda_fail(p, e, "event record");
     if (!p->plain) {
         if ((e = stage(p, 0, c, 0, p->items[0], p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
+        if ((e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
         if ((e = stage(p, 1, c, 0, p->items[1], p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        if ((e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
         if ((e = stage(p, 2, c, 0, p->items[2], p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
     } else {
         c.own_only = 1;
@@ -599,11 +624,20 @@ int psatd_push(psatd_plan_t p, const psatd_fields* f, double* gauss_dev, void* s
         }
         if ((e = stage(p, 3, c, 0, p->exch_items, 0, s)) != cudaSuccess) return cuda_fail(p, e, "exchange launch");
     }
+    if ((e = mark(3)) != cudaSuccess) return cuda_fail(p, e, "event record");
     if (p->diag && gauss_dev) {
         e = launch_gauss_reduce(c.subs, c.nsub, c.gauss_part, gauss_dev, s);
         if (e != cudaSuccess) return cuda_fail(p, e, "gauss reduce launch");
     }
     return PSATD_OK;
+}
+
+int psatd_push(psatd_plan_t p, const psatd_fields* f, double* gauss_dev, void* stream) {
+    return push_impl(p, f, gauss_dev, stream, nullptr);
+}
+
+int psatd_push_profiled(psatd_plan_t p, const psatd_fields* f, double* gauss_dev, void* stream, void* const events[4]) {
+    return push_impl(p, f, gauss_dev, stream, events);
 }
 
 int psatd_destroy(psatd_plan_t p) {

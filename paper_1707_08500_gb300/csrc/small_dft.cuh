@@ -84,6 +84,30 @@ __device__ __forceinline__ void static_for_impl(F&& f) {
 template <int N, class F>
 __device__ __forceinline__ void static_for(F&& f) { static_for_impl<0, N>(f); }
 
+// FP32 constants are split into hi + lo (lo = the FP32 rounding of the
+// remainder), so that a product with a constant carries no systematic
+// quantisation error; in FP64 the lo part is dropped.
+template <typename T>
+struct Split32 {
+    static constexpr bool kOn = sizeof(T) == 4;
+};
+template <typename T>
+constexpr T hi_of(double v) { return T(v); }
+template <typename T>
+constexpr T lo_of(double v) { return T(v - double(T(v))); }
+
+// v * (c + i s) with c, s given as (hi, lo) pairs
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul_const(cpx<T> v, T ch, T cl, T sh, T sl) {
+    if constexpr (Split32<T>::kOn) {
+        const T tr = fmaf(v.x, cl, -v.y * sl);
+        const T ti = fmaf(v.x, sl, v.y * cl);
+        return mk(fmaf(v.x, ch, fmaf(-v.y, sh, tr)), fmaf(v.x, sh, fmaf(v.y, ch, ti)));
+    } else {
+        return mk(v.x * ch - v.y * sh, v.x * sh + v.y * ch);
+    }
+}
+
 // multiply by exp(sgn 2 pi i M / N), sgn = -1 forward, +1 inverse
 template <int M, int N, bool INV, typename T>
 __device__ __forceinline__ cpx<T> twiddle(cpx<T> v) {
@@ -97,9 +121,9 @@ __device__ __forceinline__ cpx<T> twiddle(cpx<T> v) {
     } else if constexpr (4 * m == 3 * N) {      // exp(sgn i 3pi/2) = -sgn i
         return INV ? mk(v.y, -v.x) : mk(-v.y, v.x);
     } else {
-        constexpr T c = T(cos2pi(m, N));
-        constexpr T s = INV ? T(sin2pi(m, N)) : T(-sin2pi(m, N));
-        return mk(v.x * c - v.y * s, v.x * s + v.y * c);
+        constexpr double c = cos2pi(m, N);
+        constexpr double s = INV ? sin2pi(m, N) : -sin2pi(m, N);
+        return cmul_const(v, hi_of<T>(c), lo_of<T>(c), hi_of<T>(s), lo_of<T>(s));
     }
 }
 
@@ -152,17 +176,22 @@ struct DftPrime {
         v[0] = s0;
         static_for<H>([&](auto kc) {
             constexpr int k = decltype(kc)::value + 1;
-            constexpr T c1 = T(cos2pi(k, P));
-            constexpr T s1 = T(sin2pi(k, P));
-            cpx<T> R = mk(x0.x + a[0].x * c1, x0.y + a[0].y * c1);
-            cpx<T> Q = mk(b[0].x * s1, b[0].y * s1);
-            static_for<H - 1>([&](auto jc) {
-                constexpr int j = decltype(jc)::value + 2;
-                constexpr T c = T(cos2pi((long)j * k, P));
-                constexpr T s = T(sin2pi((long)j * k, P));
-                R.x += a[j - 1].x * c; R.y += a[j - 1].y * c;
-                Q.x += b[j - 1].x * s; Q.y += b[j - 1].y * s;
+            cpx<T> R = x0, Q = mk(T(0), T(0));
+            cpx<T> Rl = mk(T(0), T(0)), Ql = mk(T(0), T(0));
+            static_for<H>([&](auto jc) {
+                constexpr int j = decltype(jc)::value + 1;
+                constexpr double c = cos2pi((long)j * k, P);
+                constexpr double s = sin2pi((long)j * k, P);
+                constexpr T ch = hi_of<T>(c), sh = hi_of<T>(s);
+                R.x += a[j - 1].x * ch; R.y += a[j - 1].y * ch;
+                Q.x += b[j - 1].x * sh; Q.y += b[j - 1].y * sh;
+                if constexpr (Split32<T>::kOn) {
+                    constexpr T cl = lo_of<T>(c), sl = lo_of<T>(s);
+                    Rl.x += a[j - 1].x * cl; Rl.y += a[j - 1].y * cl;
+                    Ql.x += b[j - 1].x * sl; Ql.y += b[j - 1].y * sl;
+                }
             });
+            if constexpr (Split32<T>::kOn) { R = R + Rl; Q = Q + Ql; }
             // X_k = R + sgn i Q, X_{P-k} = R - sgn i Q
             if (INV) { v[k] = mk(R.x - Q.y, R.y + Q.x); v[P - k] = mk(R.x + Q.y, R.y - Q.x); }
             else     { v[k] = mk(R.x + Q.y, R.y - Q.x); v[P - k] = mk(R.x - Q.y, R.y + Q.x); }
