@@ -97,6 +97,20 @@ typedef struct psatd_plan_s* psatd_plan_t;
 int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
                       const psatd_sub* subs, int32_t nsub, int32_t flags);
 
+/* Tunable launch shapes of a plan (0 = library default for every field).
+ * chunk_b: (ky,kx) modes per CTA of the z/Eq. 1 stage, a power of two <= 64;
+ * f1[3]: first factor of the two-stage FFT of the x (half length), y and z
+ * axes; used for every subdomain whose length it divides with both factors
+ * in 1..16, ignored otherwise. */
+typedef struct {
+    int32_t chunk_b;
+    int32_t f1[3];
+} psatd_tuning;
+
+/* psatd_plan_create with explicit tuning (NULL = defaults). */
+int psatd_plan_create_tuned(psatd_plan_t* plan, const int32_t global_n[3], const psatd_sub* subs,
+                            int32_t nsub, int32_t flags, const psatd_tuning* tuning);
+
 /* Offset (in elements) of subdomain `sub` in every field arena, and its local
  * extents (x, y, z).  Any output pointer may be NULL. */
 int psatd_layout(psatd_plan_t plan, int32_t sub, int64_t* offset_elems, int32_t local_n[3]);

@@ -59,6 +59,7 @@ struct LaunchCommon {
     const void* subs; const void* segs; const void* tw; const void* tab; const void* tabc; void* spec;
     void* eb[6]; const void* jr[4]; double* gauss_part;
     int nsub, nseg, nf, staggered, own_only;
+    int64_t per_sub[3];   // items per subdomain of passes A, B, C when every subdomain has the same shape, else 0
 };
 
 // Coefficient table component order (each Lz*q long, position order).

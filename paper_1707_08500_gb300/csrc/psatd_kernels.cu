@@ -67,6 +67,7 @@ struct Args {
     const T* jr[4];         // Jx Jy Jz rho
     double* gauss_part;     // 2 per pass-B item
     int64_t item0, nitems;  // items handled by this launch
+    int64_t per_sub[3];     // items per subdomain of each stage when uniform, else 0
     int nsub, nseg;
     int nf;                 // fields transformed forward (9, or 10 with rho)
     int staggered;
@@ -82,28 +83,12 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
     const auto v = __ldg(reinterpret_cast<const typename vec2<T>::type*>(p));
     return mk(v.x, v.y);
 }
-template <typename T>   // streaming (evict-first) load
-__device__ __forceinline__ cpx<T> ldcs_c(const cpx<T>* p) {
-    const auto v = __ldcs(reinterpret_cast<const typename vec2<T>::type*>(p));
-    return mk(v.x, v.y);
-}
 
 template <typename T>
 struct cpx4 { T a, b, c, d; };
 template <typename T> struct vec4;
 template <> struct vec4<float> { using type = float4; };
 template <> struct vec4<double> { using type = double4; };
-template <typename T>   // streaming load of 4 consecutive reals (16-byte aligned for float)
-__device__ __forceinline__ cpx4<T> ldcs4(const T* p) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
-        return cpx4<T>{v.x, v.y, v.z, v.w};
-    } else {
-        const double2 u = __ldcs(reinterpret_cast<const double2*>(p));
-        const double2 w = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-        return cpx4<T>{u.x, u.y, w.x, w.y};
-    }
-}
 template <typename T>
 __device__ __forceinline__ void stcs4(T* p, cpx4<T> v) {
     if constexpr (sizeof(T) == 4) {
@@ -118,6 +103,32 @@ __device__ __forceinline__ void stcs_c(cpx<T>* p, cpx<T> v) {
     using V = typename vec2<T>::type;
     V w; w.x = v.x; w.y = v.y;
     __stcs(reinterpret_cast<V*>(p), w);
+}
+
+// ---- asynchronous global -> shared copies (no register staging) ------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n"
+                 :: "r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+// 16 bytes, of which the first src_bytes are read and the rest zero-filled
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
+                 :: "r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src)), "r"(src_bytes) : "memory");
+}
+// 8 bytes, of which the first src_bytes are read and the rest zero-filled
+__device__ __forceinline__ void cp_async8z(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n"
+                 :: "r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src)), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// one complex value
+template <typename T>
+__device__ __forceinline__ void cp_async_c(cpx<T>* dst, const cpx<T>* src) {
+    if constexpr (sizeof(T) == 4) cp_async8(dst, src);
+    else cp_async16(dst, src, 16);
 }
 
 // Batched transforms in shared memory.  Transform b starts at b*s_in
@@ -233,6 +244,30 @@ __device__ __forceinline__ int find_sub(const SubDesc* __restrict__ subs, int ns
     return lo;
 }
 
+
+// Decode work item `it` of a stage: warp 0 finds the subdomain (arithmetic for
+// uniform decompositions, else a binary search over the stage's first items)
+// and copies its descriptor to shared memory for the whole CTA.
+template <int STAGE, typename T>
+__device__ __forceinline__ int decode_item(const Args<T>& a, int64_t it, SubDesc* sd) {
+    __shared__ int s_sub;
+    if (threadIdx.x < 32) {
+        int s = 0;
+        if (a.per_sub[STAGE] > 0) {
+            s = int(it / a.per_sub[STAGE]);
+        } else if (threadIdx.x == 0) {
+            s = find_sub<STAGE>(a.subs, a.nsub, it);
+        }
+        s = __shfl_sync(0xffffffffu, s, 0);
+        const int* src = reinterpret_cast<const int*>(a.subs + s);
+        int* dst = reinterpret_cast<int*>(sd);
+        for (int i = threadIdx.x; i < int(sizeof(SubDesc) / 4); i += 32) dst[i] = __ldg(src + i);
+        if (threadIdx.x == 0) s_sub = s;
+    }
+    __syncthreads();
+    return s_sub;
+}
+
 template <typename T>
 __device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
     return f < 6 ? a.eb[f] : a.jr[f - 6];
@@ -243,27 +278,19 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
-        const SubDesc& d = a.subs[find_sub<0>(a.subs, a.nsub, it)];
+        decode_item<0>(a, it, &d);
         const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
         const int loc = int(it - d.itemA);
         const int f = loc / Lz, z = loc - (loc / Lz) * Lz;
         const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
         const T* src = field_in(a, f) + d.field_off + int64_t(z) * Ly * Lx;
         // packed complex z[m] = x[2m] + i x[2m+1], row y at y*pitch
-        if ((h & 1) == 0) {
-            const int h2 = h >> 1;
-            loop2(h2, Ly, [&](int y, int m) {
-                const cpx4<T> v = ldcs4(src + 4 * (y * h2 + m));
-                cpx<T>* p = sm + y * pitch + 2 * m;
-                p[0] = mk(v.a, v.b);
-                p[1] = mk(v.c, v.d);
-            });
-        } else {
-            loop2(h, Ly, [&](int y, int m) {
-                sm[y * pitch + m] = ldcs_c(reinterpret_cast<const cpx<T>*>(src) + y * h + m);
-            });
-        }
+        loop2(h, Ly, [&](int y, int m) {
+            cp_async_c(sm + y * pitch + m, reinterpret_cast<const cpx<T>*>(src) + y * h + m);
+        });
+        cp_async_wait_all();
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
         fft_fwd<false>(sm, d.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
@@ -314,9 +341,10 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
     __shared__ double red[2][kThreads / 32];
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
-        const SubDesc& d = a.subs[find_sub<1>(a.subs, a.nsub, it)];
+        decode_item<1>(a, it, &d);
         const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
         const int M = d.chunkB, lgM = d.lgB, Q = d.q, lxh = d.lxh;
         const int q0 = int(it - d.itemB) * M;
@@ -327,10 +355,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
         for (int f = 0; f < nf; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
             cpx<T>* s = sm + f * fs;
-            loop2(M, Lz, [&](int z, int m) {
-                s[z * M + m] = m < mc ? ldcs_c(src + int64_t(z) * Q + m) : mk(T(0), T(0));
-            });
+            if (sizeof(T) == 4 && (Q & 1) == 0 && M >= 2) {
+                // pairs of modes (16-byte aligned: Q, q0 and M are even),
+                // zero-filled past the ragged end of the plane
+                loop2(M >> 1, Lz, [&](int z, int m2) {
+                    const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<T>));
+                    const cpx<T>* g = src + int64_t(z) * Q + (nb ? 2 * m2 : 0);
+                    cp_async16(s + z * M + 2 * m2, g, nb);
+                });
+            } else {
+                loop2(M, Lz, [&](int z, int m) {
+                    const cpx<T>* g = src + int64_t(z) * Q + (m < mc ? m : 0);
+                    if constexpr (sizeof(T) == 4) cp_async8z(s + z * M + m, g, m < mc ? 8 : 0);
+                    else cp_async16(s + z * M + m, g, m < mc ? 16 : 0);
+                });
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
         fft_fwd<true>(sm, d.az, Batch{nf * M, 1, lgM, fs, M}, a.tw);
 
@@ -420,16 +461,17 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
-        const int s = find_sub<2>(a.subs, a.nsub, it);
-        const SubDesc& d = a.subs[s];
+        decode_item<2>(a, it, &d);
         const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
         const int nz = d.nv[2], ny = d.nv[1], ng = d.ng;
         const int loc = int(it - d.itemC);
         const int f = loc / nz, z = ng + (loc - (loc / nz) * nz);
         const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
         const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
-        loop2(lxh, Ly, [&](int y, int c) { sm[y * pitch + c] = ldcs_c(src + y * lxh + c); });
+        loop2(lxh, Ly, [&](int y, int c) { cp_async_c(sm + y * pitch + c, src + y * lxh + c); });
+        cp_async_wait_all();
         __syncthreads();
         fft_inv<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
@@ -529,6 +571,7 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     for (int i = 0; i < 4; ++i) a.jr[i] = static_cast<const T*>(c.jr[i]);
     a.gauss_part = c.gauss_part;
     a.item0 = item0;
+    for (int i = 0; i < 3; ++i) a.per_sub[i] = c.per_sub[i];
     a.nitems = nitems;
     a.nsub = c.nsub;
     a.nseg = c.nseg;

@@ -134,6 +134,7 @@ struct psatd_plan_s {
     int64_t n_tab = 0, n_tabc = 0;
     int64_t items[3] = {0, 0, 0};
     int64_t exch_items = 0;
+    int64_t per_sub[3] = {0, 0, 0};   // items per subdomain when uniform
     int smemA = 0, smemB = 0, smemC = 0;
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_spec = 0, ws_need = 0;
@@ -172,7 +173,17 @@ const char* psatd_status_string(int s) {
 const char* psatd_last_error(psatd_plan_t p) { return p ? p->err.c_str() : "null plan"; }
 
 int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub, int32_t flags) {
+    return psatd_plan_create_tuned(out, global_n, subs, nsub, flags, nullptr);
+}
+
+int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub,
+                            int32_t flags, const psatd_tuning* tuning) {
     if (!out || !global_n || !subs || nsub <= 0) return PSATD_E_ARG;
+    if (tuning) {
+        const int cb = tuning->chunk_b;
+        if (cb < 0 || cb > 64 || (cb & (cb - 1))) return PSATD_E_ARG;
+        for (int a = 0; a < 3; ++a) if (tuning->f1[a] < 0 || tuning->f1[a] > kMaxDft) return PSATD_E_ARG;
+    }
     *out = nullptr;
     psatd_plan_s* p = new (std::nothrow) psatd_plan_s();
     if (!p) return PSATD_E_ARG;
@@ -237,6 +248,14 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
         int h = d.L[0] / 2;
         if (!factor(h, d.ax.f1, d.ax.f2) || !factor(d.L[1], d.ay.f1, d.ay.f2) || !factor(d.L[2], d.az.f1, d.az.f2))
             return bad(PSATD_E_UNSUPPORTED, "subdomain " + std::to_string(s) + ": local length is not a product of two factors <= 16");
+        if (tuning) {
+            AxisPlan* ap[3] = {&d.ax, &d.ay, &d.az};
+            const int len[3] = {h, d.L[1], d.L[2]};
+            for (int a = 0; a < 3; ++a) {
+                const int f = tuning->f1[a];
+                if (f > 0 && len[a] % f == 0 && len[a] / f <= kMaxDft) { ap[a]->f1 = f; ap[a]->f2 = len[a] / f; }
+            }
+        }
         d.ax.n = h; d.ay.n = d.L[1]; d.az.n = d.L[2];
         d.lxh = h + 1;
         d.pitch = d.lxh | 1;
@@ -297,8 +316,8 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
     int64_t iA = 0, iB = 0, iC = 0, spec = 0, maxspec = 0;
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
-        int M = p->f64 ? 4 : 8;
-        while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 100 * 1024) M /= 2;
+        int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
+        while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
         d.chunkB = M;
         d.lgB = 0;
         while ((1 << d.lgB) < M) ++d.lgB;
@@ -319,6 +338,17 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
         maxspec = std::max<int64_t>(maxspec, int64_t(align_up(sp, 32)));
     }
     p->items[0] = iA; p->items[1] = iB; p->items[2] = iC;
+    {
+        bool uni = true;
+        const SubDesc& d0 = p->desc[0];
+        for (const SubDesc& d : p->desc)
+            uni = uni && d.L[0] == d0.L[0] && d.L[1] == d0.L[1] && d.L[2] == d0.L[2] && d.nv[2] == d0.nv[2] && d.chunkB == d0.chunkB;
+        if (uni) {
+            p->per_sub[0] = int64_t(p->nf) * d0.L[2];
+            p->per_sub[1] = (d0.q + d0.chunkB - 1) / d0.chunkB;
+            p->per_sub[2] = 6 * int64_t(d0.nv[2]);
+        }
+    }
     p->spec_elems = p->plain ? maxspec : spec;
     if (std::max(p->smemA, p->smemB) > 227 * 1024)
         return bad(PSATD_E_UNSUPPORTED, "a local plane does not fit in shared memory");
@@ -575,6 +605,7 @@ static LaunchCommon common(psatd_plan_s* p, const psatd_fields* f) {
     c.nf = p->nf;
     c.staggered = p->stag ? 1 : 0;
     c.own_only = 0;
+    for (int i = 0; i < 3; ++i) c.per_sub[i] = p->per_sub[i];
     return c;
 }
 

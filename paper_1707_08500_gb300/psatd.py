@@ -16,7 +16,7 @@ import torch
 from . import inputs as _inputs
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpsatd.so")
+LIB_PATH = os.environ.get("PSATD_LIB") or os.path.join(_HERE, "libpsatd.so")
 
 PSATD_F32 = 0x01
 PSATD_F64 = 0x02
@@ -30,7 +30,7 @@ STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NO
 EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
-           "psatd_push_profiled")
+           "psatd_push_profiled", "psatd_plan_create_tuned")
 
 
 class PsatdError(RuntimeError):
@@ -42,6 +42,10 @@ class PsatdError(RuntimeError):
 class SubT(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_int32 * 3), ("n", ctypes.c_int32 * 3),
                 ("ng", ctypes.c_int32), ("order", ctypes.c_int32)]
+
+
+class TuningT(ctypes.Structure):
+    _fields_ = [("chunk_b", ctypes.c_int32), ("f1", ctypes.c_int32 * 3)]
 
 
 class FieldsT(ctypes.Structure):
@@ -61,6 +65,8 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         P, I32, I64, VP = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         L.psatd_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(SubT), I32, I32]
+        L.psatd_plan_create_tuned.argtypes = [ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(SubT), I32, I32,
+                                              ctypes.POINTER(TuningT)]
         L.psatd_layout.argtypes = [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32)]
         L.psatd_arena_elems.argtypes = [P, ctypes.POINTER(I64)]
         L.psatd_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
@@ -89,7 +95,8 @@ def _check(code: int, plan=None):
 
 
 # ---- thin wrappers with the C names -------------------------------------------
-def psatd_plan_create(global_n: Sequence[int], subs: Sequence, flags: int) -> ctypes.c_void_p:
+def psatd_plan_create(global_n: Sequence[int], subs: Sequence, flags: int, tuning: Optional[dict] = None) -> ctypes.c_void_p:
+    """tuning: None or {"chunk_b": M, "f1": (fx, fy, fz)} (0 = default)."""
     arr = (SubT * len(subs))()
     for i, s in enumerate(subs):
         arr[i].lo[:] = list(s.lo)
@@ -98,7 +105,13 @@ def psatd_plan_create(global_n: Sequence[int], subs: Sequence, flags: int) -> ct
         arr[i].order = s.p
     g = (ctypes.c_int32 * 3)(*global_n)
     h = ctypes.c_void_p()
-    code = lib().psatd_plan_create(ctypes.byref(h), g, arr, len(subs), flags)
+    if tuning is None:
+        code = lib().psatd_plan_create(ctypes.byref(h), g, arr, len(subs), flags)
+    else:
+        t = TuningT()
+        t.chunk_b = int(tuning.get("chunk_b", 0))
+        t.f1[:] = [int(v) for v in tuning.get("f1", (0, 0, 0))]
+        code = lib().psatd_plan_create_tuned(ctypes.byref(h), g, arr, len(subs), flags, ctypes.byref(t))
     if code != 0:
         raise PsatdError(code, lib().psatd_status_string(code).decode())
     return h
@@ -184,7 +197,7 @@ class Solver:
     at ``layout[s][0]`` as a dense [Lz][Ly][Lx] box."""
 
     def __init__(self, wl: "_inputs.Workload", precision: Optional[str] = None, plain: bool = False,
-                 gauss: bool = False, device="cuda"):
+                 gauss: bool = False, device="cuda", tuning: Optional[dict] = None):
         self.wl = wl
         self.precision = precision or wl.precision
         self.dtype = torch.float64 if self.precision == "f64" else torch.float32
@@ -198,7 +211,8 @@ class Solver:
         self.flags = flags
         self.gauss = gauss
         self.device = torch.device(device)
-        self.plan = psatd_plan_create(wl.global_n, wl.subs, flags)
+        self.tuning = tuning
+        self.plan = psatd_plan_create(wl.global_n, wl.subs, flags, tuning)
         self.layout = [psatd_layout(self.plan, s) for s in range(len(wl.subs))]
         self.arena_elems = psatd_arena_elems(self.plan)
         self.ws_bytes = psatd_workspace_bytes(self.plan)

@@ -1,0 +1,138 @@
+"""Autotuner for the launch shapes of a plan (chunk width of the z/Eq. 1 stage
+and the two-factor split of every FFT axis).
+
+Each candidate is a plan built with psatd_plan_create_tuned on the same field
+arenas; it is timed per stage with psatd_push_profiled (CUDA events on the
+launching stream).  The search is a coordinate descent: the z factor and the
+chunk width only change pass B; the x and y factors change passes A and C.
+Results are cached in a JSON file keyed by the decomposition signature,
+precision, flags and GPU name.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import Dict, List, Optional
+
+import torch
+
+from . import inputs as I
+from . import psatd as P
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def _divisor_splits(n: int) -> List[int]:
+    return [f for f in range(1, 17) if n % f == 0 and n // f <= 16]
+
+
+def signature(wl: I.Workload, flags: int) -> str:
+    h = hashlib.sha256()
+    h.update(repr((wl.global_n, [(s.lo, s.n, s.ng, s.p) for s in wl.subs], flags)).encode())
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{wl.name}:{name}:{h.hexdigest()[:16]}"
+
+
+class _Bench:
+    """One set of arenas and a workspace reused by every candidate plan."""
+
+    def __init__(self, wl: I.Workload, flags: int, device):
+        self.wl, self.flags, self.device = wl, flags, torch.device(device)
+        dt = torch.float64 if flags & P.PSATD_F64 else torch.float32
+        h = P.psatd_plan_create(wl.global_n, wl.subs, flags)
+        n = P.psatd_arena_elems(h)
+        P.psatd_destroy(h)
+        g = torch.Generator(device=self.device).manual_seed(1707)
+        self.arenas = {k: torch.randn(n, generator=g, device=self.device, dtype=dt) for k in I.FIELD_NAMES}
+        self.fields = P.make_fields([self.arenas[k] for k in ("Ex", "Ey", "Ez")],
+                                    [self.arenas[k] for k in ("Bx", "By", "Bz")],
+                                    [self.arenas[k] for k in ("Jx", "Jy", "Jz")], self.arenas["rho"])
+        self.ws = None
+        self.gauss = torch.zeros(2 * len(wl.subs), dtype=torch.float64, device=self.device) \
+            if flags & P.PSATD_GAUSS_DIAG else None
+
+    def time(self, tuning: Dict, reps: int = 3) -> Optional[List[float]]:
+        try:
+            h = P.psatd_plan_create(self.wl.global_n, self.wl.subs, self.flags, tuning)
+        except P.PsatdError:
+            return None
+        try:
+            nb = P.psatd_workspace_bytes(h)
+            if self.ws is None or self.ws.numel() < nb + 256:
+                self.ws = None
+                torch.cuda.empty_cache()
+                self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+            ptr = (self.ws.data_ptr() + 255) // 256 * 256
+            P.psatd_set_workspace(h, ptr, nb)
+            P.psatd_set_coeffs(h, self.wl.c_dt, self.wl.dx)
+            st = torch.cuda.current_stream(self.device)
+            gp = self.gauss.data_ptr() if self.gauss is not None else None
+            P.psatd_push(h, self.fields, gp, st.cuda_stream)          # warm-up
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+            for e in evs:
+                for x in e:
+                    x.record(st)
+            torch.cuda.synchronize()
+            for k in range(reps):
+                P.psatd_push_profiled(h, self.fields, gp, st.cuda_stream, [x.cuda_event for x in evs[k]])
+            torch.cuda.synchronize()
+            return [min(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(reps)) for i in range(3)]
+        finally:
+            P.psatd_destroy(h)
+
+
+def autotune(wl: I.Workload, flags: int, device="cuda", reps: int = 3, use_cache: bool = True,
+             verbose: bool = False) -> Dict:
+    """Best tuning found for the workload (dict for psatd_plan_create_tuned)."""
+    key = signature(wl, flags)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            with open(CACHE) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+        if key in cache:
+            return cache[key]["tuning"]
+    b = _Bench(wl, flags, device)
+    sd = max(set(s.local for s in wl.subs), key=lambda L: sum(1 for s in wl.subs if s.local == L))
+    lens = (sd[0] // 2, sd[1], sd[2])
+    best = {"chunk_b": 0, "f1": [0, 0, 0]}
+    t0 = b.time(best, reps)
+    log = [("default", best, t0)]
+    # pass B: z split and chunk width
+    bestB, bestT = None, None
+    for fz in _divisor_splits(lens[2]):
+        for M in (2, 4, 8, 16, 32):
+            cand = {"chunk_b": M, "f1": [0, 0, fz]}
+            t = b.time(cand, reps)
+            log.append(("B", cand, t))
+            if t and (bestT is None or t[1] < bestT):
+                bestB, bestT = cand, t[1]
+    if bestB:
+        best["chunk_b"], best["f1"][2] = bestB["chunk_b"], bestB["f1"][2]
+    # passes A and C: x then y split
+    for ax in (0, 1):
+        bestAC, bestf = None, None
+        for f in _divisor_splits(lens[ax]):
+            cand = {"chunk_b": best["chunk_b"], "f1": list(best["f1"])}
+            cand["f1"][ax] = f
+            t = b.time(cand, reps)
+            log.append((("x", "y")[ax], cand, t))
+            if t and (bestAC is None or t[0] + t[2] < bestAC):
+                bestAC, bestf = t[0] + t[2], f
+        if bestf:
+            best["f1"][ax] = bestf
+    tb = b.time(best, reps)
+    if verbose:
+        for name, cand, t in log:
+            print(name, cand, t)
+        print("best", best, tb, "default", t0)
+    if use_cache:
+        cache[key] = {"tuning": best, "stage_ms": tb, "default_stage_ms": t0}
+        tmp = CACHE + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, CACHE)
+    return best
