@@ -6,6 +6,7 @@ namespace psatd {
 
 constexpr int kMaxDft = 16;       // largest register DFT
 constexpr int kThreads = 256;     // threads per CTA of every stage kernel
+constexpr int kSegSmem = 64;      // exchange segments staged in shared memory per CTA
 
 // One local FFT axis of length n = f1 * f2, done as two register stages.
 // Forward output (and inverse input) is in "position" order: frequency

@@ -227,7 +227,16 @@ __device__ __forceinline__ void fft_inv(cpx<T>* sm, const AxisPlan& ax, const Ba
     __syncthreads();
 }
 
-__device__ __forceinline__ int xpos(int k, const AxisPlan& a) { return (k % a.f1) * a.f2 + k / a.f1; }
+// Pairs (k, h-k) of the real split in the position order of an h = f1*f2
+// transform (frequency k1 + f1 k2 at position k1 f2 + k2).  Pair 0 is k = 0;
+// pairs 1..f2/2 pair position P with f2 - P (k1 = 0); the remaining pairs
+// pair P >= f2 with h + f2 - 1 - P.  Every unordered pair appears once.
+__device__ __forceinline__ int split_pairs(int h, int f2) { return 1 + f2 / 2 + (h - f2 + 1) / 2; }
+__device__ __forceinline__ void split_pair(int i, int h, int f2, int& pa, int& pb) {
+    const int lower = f2 / 2;
+    if (i <= lower) { pa = i; pb = f2 - i; }
+    else { pa = f2 + (i - lower - 1); pb = h + f2 - 1 - pa; }
+}
 
 template <int STAGE>
 __device__ __forceinline__ int64_t stage_item(const SubDesc& d) {
@@ -294,21 +303,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Arg
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
         fft_fwd<false>(sm, d.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
-        // split the packed transform into the half spectrum X[0..h]
+        // split the packed transform into the half spectrum X[0..h], walking
+        // the pairs (k, h-k) directly in position order (see split_pair)
         const twd<T>* wp = a.tw + d.tw_post;
-        loop2(Ly, h / 2 + 1, [&](int k, int y) {
+        const int f2x = d.ax.f2;
+        loop2(Ly, split_pairs(h, f2x), [&](int i, int y) {
             cpx<T>* p = sm + y * pitch;
-            if (k == 0) {
+            if (i == 0) {
                 const cpx<T> z0 = p[0];
                 p[0] = mk(z0.x + z0.y, T(0));
                 p[h] = mk(z0.x - z0.y, T(0));
             } else {
-                const int pa = xpos(k, d.ax), pb = xpos(h - k, d.ax);
+                int pa, pb;
+                split_pair(i, h, f2x, pa, pb);
                 const cpx<T> A = p[pa], Bc = conj(p[pb]);
                 const cpx<T> e = scale(A + Bc, T(0.5));
                 const cpx<T> dd = A - Bc;
                 const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);   // (A - conj B)/(2i)
-                const cpx<T> wo = mul_tw(o, ld_tw(wp + k));
+                const cpx<T> wo = mul_tw(o, ld_tw(wp + pa));
                 p[pa] = e + wo;
                 if (pb != pa) p[pb] = conj(e - wo);
             }
@@ -462,6 +474,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
+    __shared__ Segment segs[kSegSmem];
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
         decode_item<2>(a, it, &d);
         const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
@@ -471,22 +484,31 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
         const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
         const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
         loop2(lxh, Ly, [&](int y, int c) { cp_async_c(sm + y * pitch + c, src + y * lxh + c); });
+        // this subdomain's exchange segments (the first kSegSmem of them)
+        const int nsg = min(d.seg_end - d.seg_begin, kSegSmem);
+        {
+            const int* gs = reinterpret_cast<const int*>(a.segs + d.seg_begin);
+            int* ss = reinterpret_cast<int*>(segs);
+            for (int i = threadIdx.x; i < nsg * int(sizeof(Segment) / 4); i += kThreads) ss[i] = __ldg(gs + i);
+        }
         cp_async_wait_all();
         __syncthreads();
         fft_inv<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
         const twd<T>* wp = a.tw + d.tw_post;
+        const int f2x = d.ax.f2;
         cpx<T>* rows = sm + ng * pitch;
-        loop2(ny, h / 2 + 1, [&](int k, int y) {
+        loop2(ny, split_pairs(h, f2x), [&](int i, int y) {
             cpx<T>* p = rows + y * pitch;
-            if (k == 0) {
+            if (i == 0) {
                 const T x0 = p[0].x, xh = p[h].x;        // real parts only (C2R)
                 p[0] = mk(x0 + xh, x0 - xh);
             } else {
-                const int pa = xpos(k, d.ax), pb = xpos(h - k, d.ax);
+                int pa, pb;
+                split_pair(i, h, f2x, pa, pb);
                 const cpx<T> A = p[pa], Bc = conj(p[pb]);
                 const cpx<T> e = A + Bc;
-                const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + k));
+                const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + pa));
                 p[pa] = e + mul_i(o);
                 if (pb != pa) p[pb] = conj(e) + mul_i(conj(o));
             }
@@ -497,8 +519,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
         T* out = a.eb[f];
         const T* rp = reinterpret_cast<const T*>(sm);
         const int rs = 2 * pitch;                         // real row stride
-        for (int g = d.seg_begin; g < d.seg_end; ++g) {
-            const Segment& sg = a.segs[g];
+        for (int g = 0; g < d.seg_end - d.seg_begin; ++g) {
+            const Segment& sg = g < kSegSmem ? segs[g] : a.segs[d.seg_begin + g];
             if (a.own_only && !sg.identity) continue;
             if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
             T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;

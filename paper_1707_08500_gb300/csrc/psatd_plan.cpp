@@ -279,13 +279,16 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         d.ay.tw = add_tw(d.ay.n);
         d.az.tw = add_tw(d.az.n);
     }
+    // real-split twiddles exp(-2 pi i k/Lx) stored in the position order of the
+    // x transform (entry P holds k = P/f2 + f1*(P%f2)), one table per (Lx, f1)
     for (auto& d : p->desc) {
-        auto it = p->post_off.find(d.L[0]);
+        const int key = d.L[0] * 32 + d.ax.f1;
+        auto it = p->post_off.find(key);
         if (it == p->post_off.end()) {
-            p->post_off[d.L[0]] = int(p->n_tw);
-            p->n_tw += d.L[0] / 2 + 1;
+            p->post_off[key] = int(p->n_tw);
+            p->n_tw += d.ax.n;
         }
-        d.tw_post = p->post_off[d.L[0]];
+        d.tw_post = p->post_off[key];
     }
     // --- coefficient tables, one set per (shape, order, factorisation) ----------
     for (int s = 0; s < nsub; ++s) {
@@ -464,8 +467,10 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
     std::vector<cd> tw(size_t(p->n_tw));
     for (auto& kv : p->tw_off)
         for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
-    for (auto& kv : p->post_off)
-        for (int k = 0; k <= kv.first / 2; ++k) tw[kv.second + k] = unit_root(k, kv.first);
+    for (auto& kv : p->post_off) {
+        const int Lx = kv.first / 32, f1 = kv.first % 32, h = Lx / 2, f2 = h / f1;
+        for (int P = 0; P < h; ++P) tw[kv.second + P] = unit_root(P / f2 + f1 * (P % f2), Lx);
+    }
     // each twiddle is stored as (hi, lo): in FP32 lo is the rounding of the
     // remainder so that hi + lo carries the FP64 value; in FP64 lo = 0
     if (p->f64) {
