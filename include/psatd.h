@@ -154,6 +154,36 @@ int psatd_push(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev,
 int psatd_push_profiled(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev, void* stream,
                         void* const events[4]);
 
+/* Size of the device buffer behind psatd_push_static (32 MiB). */
+#define PSATD_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
+
+/* psatd_push for callers that cannot allocate device memory.  (The paper has
+ * no counterpart; this is a convenience of the library.)  Some callers may
+ * not call cudaMalloc: a plugin hosted by an application that owns every
+ * device allocation and gives it no allocator, or a code path where a
+ * cudaMalloc -- which can synchronise the whole device -- is not allowed.
+ * Such callers still pass their field arenas and optional Gauss output, but
+ * no workspace: the push runs the same kernels on a workspace held in one
+ * library-owned, file-scope device array of PSATD_STATIC_WORKSPACE_BYTES that
+ * every GPU which loads the library keeps until the process exits.
+ *
+ * c_dt and dx are the parameters otherwise given to psatd_set_coeffs; the
+ * plan needs neither psatd_set_workspace nor psatd_set_coeffs.  Plans whose
+ * psatd_workspace_bytes exceeds PSATD_STATIC_WORKSPACE_BYTES are rejected
+ * with PSATD_E_NOMEM.  Each call first copies the plan's descriptors and
+ * Eq. 1 tables into that array (stream-ordered on `stream`), then enqueues
+ * the stages; it allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  Every call and every plan share the one array per
+ * device, which keeps the last call's contents: no region of it needs to
+ * start at zero, because each call rewrites everything it reads before
+ * reading it.  Calls that overlap on the GPU (different streams or threads
+ * without ordering) race on the array.  The first call on each device looks
+ * the array's device address up once (with that device current); make that
+ * first call before any stream capture.  A call on a device whose context was
+ * reset after that lookup is not supported. */
+int psatd_push_static(psatd_plan_t plan, double c_dt, const double dx[3], const psatd_fields* fields,
+                      double* gauss_dev, void* stream);
+
 /* Copy every valid cell into each guard cell that images it (all 26
  * neighbour directions, periodic wrap), for E and B only, on `stream`. */
 int psatd_exchange_guards(psatd_plan_t plan, const psatd_fields* fields, void* stream);

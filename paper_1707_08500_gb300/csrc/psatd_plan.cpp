@@ -143,6 +143,10 @@ struct psatd_plan_s {
     size_t ws_size = 0;
     bool coeffs = false;
     std::string err;
+    // host images for pushes into library-owned device memory (push_into)
+    bool img_valid = false;
+    double img_c_dt = 0, img_dx[3] = {0, 0, 0};
+    std::vector<char> img_tw, img_tab, img_tabc;
 };
 
 static int fail(psatd_plan_s* p, int code, const std::string& msg) {
@@ -152,6 +156,117 @@ static int fail(psatd_plan_s* p, int code, const std::string& msg) {
 
 static int cuda_fail(psatd_plan_s* p, cudaError_t e, const char* where) {
     return fail(p, PSATD_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Device image of the twiddle pool: exp(-2 pi i m/n) per transform length and
+// the real-split twiddles exp(-2 pi i k/Lx) in position order.
+static std::vector<char> twiddle_image(const psatd_plan_s* p) {
+    std::vector<cd> tw(size_t(p->n_tw));
+    for (auto& kv : p->tw_off)
+        for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
+    for (auto& kv : p->post_off) {
+        const int Lx = kv.first / 32, f1 = kv.first % 32, h = Lx / 2, f2 = h / f1;
+        for (int P = 0; P < h; ++P) tw[kv.second + P] = unit_root(P / f2 + f1 * (P % f2), Lx);
+    }
+    // each twiddle is stored as (hi, lo): in FP32 lo is the rounding of the
+    // remainder so that hi + lo carries the FP64 value; in FP64 lo = 0
+    std::vector<char> out;
+    if (p->f64) {
+        std::vector<double> t64(tw.size() * 4, 0.0);
+        for (size_t i = 0; i < tw.size(); ++i) { t64[4 * i] = tw[i].real(); t64[4 * i + 1] = tw[i].imag(); }
+        out.assign(reinterpret_cast<const char*>(t64.data()), reinterpret_cast<const char*>(t64.data() + t64.size()));
+    } else {
+        std::vector<float> t32(tw.size() * 4);
+        for (size_t i = 0; i < tw.size(); ++i) {
+            const float hr = float(tw[i].real()), hi = float(tw[i].imag());
+            t32[4 * i] = hr;
+            t32[4 * i + 1] = hi;
+            t32[4 * i + 2] = float(tw[i].real() - double(hr));
+            t32[4 * i + 3] = float(tw[i].imag() - double(hi));
+        }
+        out.assign(reinterpret_cast<const char*>(t32.data()), reinterpret_cast<const char*>(t32.data() + t32.size()));
+    }
+    return out;
+}
+
+// Device images of the Eq. 1 coefficient tables (real part) and of the
+// stagger phases (complex part) for c_dt and dx, built in FP64 and stored in
+// the plan's precision.
+static void table_images(const psatd_plan_s* p, double c_dt, const double dx[3], std::vector<char>& out_tab,
+                         std::vector<char>& out_tabc) {
+    std::vector<double> tab(size_t(p->n_tab), 0.0);
+    std::vector<cd> tabc(size_t(std::max<int64_t>(p->n_tabc, 1)));
+    for (size_t ti = 0; ti < p->tab_keys.size(); ++ti) {
+        const auto& key = p->tab_keys[ti];
+        const int L[3] = {key.Lx, key.Ly, key.Lz};
+        const int h = L[0] / 2, lxh = h + 1, q = L[1] * lxh;
+        const int f1[3] = {key.f1x, key.f1y, key.f1z};
+        const int n[3] = {h, L[1], L[2]};
+        // natural index held at each position of an axis (position order of the
+        // forward transforms: frequency k1 + f1 k2 at position k1 f2 + k2)
+        std::vector<int> nat[3];
+        for (int a = 0; a < 3; ++a) {
+            int f2 = n[a] / f1[a];
+            int len = a == 0 ? lxh : n[a];
+            nat[a].resize(len);
+            for (int P = 0; P < n[a]; ++P) nat[a][P] = P / f2 + f1[a] * (P % f2);
+            if (a == 0) nat[0][h] = h;
+        }
+        std::vector<double> km[3];
+        for (int a = 0; a < 3; ++a) {
+            km[a].resize(nat[a].size());
+            for (size_t P = 0; P < nat[a].size(); ++P) km[a][P] = kmod(nat[a][P], L[a], dx[a], key.p, p->stag);
+        }
+        double* tk = tab.data() + p->tab_k_off[ti];
+        for (int P = 0; P < lxh; ++P) tk[P] = km[0][P];
+        for (int P = 0; P < L[1]; ++P) tk[lxh + P] = km[1][P];
+        for (int P = 0; P < L[2]; ++P) tk[lxh + L[1] + P] = km[2][P];
+        if (p->stag) {
+            cd* ph = tabc.data() + p->tab_ph_off[ti];
+            for (int P = 0; P < lxh; ++P) ph[P] = std::exp(cd(0, -kexact(nat[0][P], L[0], dx[0]) * dx[0] / 2));
+            for (int P = 0; P < L[1]; ++P) ph[lxh + P] = std::exp(cd(0, -kexact(nat[1][P], L[1], dx[1]) * dx[1] / 2));
+            for (int P = 0; P < L[2]; ++P) ph[lxh + L[1] + P] = std::exp(cd(0, -kexact(nat[2][P], L[2], dx[2]) * dx[2] / 2));
+        }
+        // Eq. 1 coefficients per mode, scaled by 1/(Lx Ly Lz) (the inverse
+        // transforms are unnormalised); 1/|k| is not scaled
+        const double invN = 1.0 / (double(L[0]) * L[1] * L[2]);
+        const int64_t NM = int64_t(L[2]) * q;
+        double* tc = tab.data() + p->tab_coef_off[ti];
+        for (int zp = 0; zp < L[2]; ++zp)
+            for (int yp = 0; yp < L[1]; ++yp)
+                for (int xp = 0; xp < lxh; ++xp) {
+                    const double kx = km[0][xp], ky = km[1][yp], kz = km[2][zp];
+                    const double k = std::sqrt(kx * kx + ky * ky + kz * kz);
+                    const double x = k * c_dt;
+                    const double C = std::cos(x), S = std::sin(x);
+                    const double omc = 2.0 * std::sin(x / 2) * std::sin(x / 2);
+                    double Sk, omck, dk, inv;
+                    if (k > 0) {
+                        Sk = S / k; omck = omc / k; inv = 1.0 / k;
+                        dk = (std::fabs(x) < 1e-3) ? c_dt * (-x * x / 6.0 + x * x * x * x / 120.0) : Sk - c_dt;
+                    } else {
+                        Sk = c_dt; omck = 0.0; inv = 0.0; dk = 0.0;
+                    }
+                    const int64_t i = int64_t(zp) * q + int64_t(yp) * lxh + xp;
+                    tc[TAB_C * NM + i] = C * invN;
+                    tc[TAB_S * NM + i] = S * invN;
+                    tc[TAB_SK * NM + i] = Sk * invN;
+                    tc[TAB_OMC * NM + i] = omc * invN;
+                    tc[TAB_OMCK * NM + i] = omck * invN;
+                    tc[TAB_DK * NM + i] = dk * invN;
+                    tc[TAB_INVK * NM + i] = inv;
+                }
+    }
+    if (p->f64) {
+        out_tab.assign(reinterpret_cast<const char*>(tab.data()), reinterpret_cast<const char*>(tab.data() + tab.size()));
+        out_tabc.assign(reinterpret_cast<const char*>(tabc.data()), reinterpret_cast<const char*>(tabc.data() + size_t(p->n_tabc)));
+    } else {
+        std::vector<float> t32(tab.begin(), tab.end());
+        out_tab.assign(reinterpret_cast<const char*>(t32.data()), reinterpret_cast<const char*>(t32.data() + t32.size()));
+        std::vector<float> c32(size_t(p->n_tabc) * 2);
+        for (int64_t i = 0; i < p->n_tabc; ++i) { c32[2 * i] = float(tabc[i].real()); c32[2 * i + 1] = float(tabc[i].imag()); }
+        out_tabc.assign(reinterpret_cast<const char*>(c32.data()), reinterpret_cast<const char*>(c32.data() + c32.size()));
+    }
 }
 
 extern "C" {
@@ -463,30 +578,9 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
         e = cudaMemcpy(p->ws + p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy segments"); }
     }
-    // twiddles exp(-2 pi i m/n) and the real-split twiddles exp(-2 pi i k/Lx)
-    std::vector<cd> tw(size_t(p->n_tw));
-    for (auto& kv : p->tw_off)
-        for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
-    for (auto& kv : p->post_off) {
-        const int Lx = kv.first / 32, f1 = kv.first % 32, h = Lx / 2, f2 = h / f1;
-        for (int P = 0; P < h; ++P) tw[kv.second + P] = unit_root(P / f2 + f1 * (P % f2), Lx);
-    }
-    // each twiddle is stored as (hi, lo): in FP32 lo is the rounding of the
-    // remainder so that hi + lo carries the FP64 value; in FP64 lo = 0
-    if (p->f64) {
-        std::vector<double> t64(tw.size() * 4, 0.0);
-        for (size_t i = 0; i < tw.size(); ++i) { t64[4 * i] = tw[i].real(); t64[4 * i + 1] = tw[i].imag(); }
-        e = cudaMemcpy(p->ws + p->off_tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> t32(tw.size() * 4);
-        for (size_t i = 0; i < tw.size(); ++i) {
-            const float hr = float(tw[i].real()), hi = float(tw[i].imag());
-            t32[4 * i] = hr;
-            t32[4 * i + 1] = hi;
-            t32[4 * i + 2] = float(tw[i].real() - double(hr));
-            t32[4 * i + 3] = float(tw[i].imag() - double(hi));
-        }
-        e = cudaMemcpy(p->ws + p->off_tw, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    {
+        const std::vector<char> tw = twiddle_image(p);
+        e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
     return PSATD_OK;
@@ -496,83 +590,11 @@ int psatd_set_coeffs(psatd_plan_t p, double c_dt, const double dx[3]) {
     if (!p || !dx) return PSATD_E_ARG;
     if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
     if (!(c_dt == c_dt) || !(dx[0] > 0 && dx[1] > 0 && dx[2] > 0)) return fail(p, PSATD_E_ARG, "bad c_dt or dx");
-    std::vector<double> tab(size_t(p->n_tab), 0.0);
-    std::vector<cd> tabc(size_t(std::max<int64_t>(p->n_tabc, 1)));
-    for (size_t ti = 0; ti < p->tab_keys.size(); ++ti) {
-        const auto& key = p->tab_keys[ti];
-        const int L[3] = {key.Lx, key.Ly, key.Lz};
-        const int h = L[0] / 2, lxh = h + 1, q = L[1] * lxh;
-        const int f1[3] = {key.f1x, key.f1y, key.f1z};
-        const int n[3] = {h, L[1], L[2]};
-        // natural index held at each position of an axis (position order of the
-        // forward transforms: frequency k1 + f1 k2 at position k1 f2 + k2)
-        std::vector<int> nat[3];
-        for (int a = 0; a < 3; ++a) {
-            int f2 = n[a] / f1[a];
-            int len = a == 0 ? lxh : n[a];
-            nat[a].resize(len);
-            for (int P = 0; P < n[a]; ++P) nat[a][P] = P / f2 + f1[a] * (P % f2);
-            if (a == 0) nat[0][h] = h;
-        }
-        std::vector<double> km[3];
-        for (int a = 0; a < 3; ++a) {
-            km[a].resize(nat[a].size());
-            for (size_t P = 0; P < nat[a].size(); ++P) km[a][P] = kmod(nat[a][P], L[a], dx[a], key.p, p->stag);
-        }
-        double* tk = tab.data() + p->tab_k_off[ti];
-        for (int P = 0; P < lxh; ++P) tk[P] = km[0][P];
-        for (int P = 0; P < L[1]; ++P) tk[lxh + P] = km[1][P];
-        for (int P = 0; P < L[2]; ++P) tk[lxh + L[1] + P] = km[2][P];
-        if (p->stag) {
-            cd* ph = tabc.data() + p->tab_ph_off[ti];
-            for (int P = 0; P < lxh; ++P) ph[P] = std::exp(cd(0, -kexact(nat[0][P], L[0], dx[0]) * dx[0] / 2));
-            for (int P = 0; P < L[1]; ++P) ph[lxh + P] = std::exp(cd(0, -kexact(nat[1][P], L[1], dx[1]) * dx[1] / 2));
-            for (int P = 0; P < L[2]; ++P) ph[lxh + L[1] + P] = std::exp(cd(0, -kexact(nat[2][P], L[2], dx[2]) * dx[2] / 2));
-        }
-        // Eq. 1 coefficients per mode, scaled by 1/(Lx Ly Lz) (the inverse
-        // transforms are unnormalised); 1/|k| is not scaled
-        const double invN = 1.0 / (double(L[0]) * L[1] * L[2]);
-        const int64_t NM = int64_t(L[2]) * q;
-        double* tc = tab.data() + p->tab_coef_off[ti];
-        for (int zp = 0; zp < L[2]; ++zp)
-            for (int yp = 0; yp < L[1]; ++yp)
-                for (int xp = 0; xp < lxh; ++xp) {
-                    const double kx = km[0][xp], ky = km[1][yp], kz = km[2][zp];
-                    const double k = std::sqrt(kx * kx + ky * ky + kz * kz);
-                    const double x = k * c_dt;
-                    const double C = std::cos(x), S = std::sin(x);
-                    const double omc = 2.0 * std::sin(x / 2) * std::sin(x / 2);
-                    double Sk, omck, dk, inv;
-                    if (k > 0) {
-                        Sk = S / k; omck = omc / k; inv = 1.0 / k;
-                        dk = (std::fabs(x) < 1e-3) ? c_dt * (-x * x / 6.0 + x * x * x * x / 120.0) : Sk - c_dt;
-                    } else {
-                        Sk = c_dt; omck = 0.0; inv = 0.0; dk = 0.0;
-                    }
-                    const int64_t i = int64_t(zp) * q + int64_t(yp) * lxh + xp;
-                    tc[TAB_C * NM + i] = C * invN;
-                    tc[TAB_S * NM + i] = S * invN;
-                    tc[TAB_SK * NM + i] = Sk * invN;
-                    tc[TAB_OMC * NM + i] = omc * invN;
-                    tc[TAB_OMCK * NM + i] = omck * invN;
-                    tc[TAB_DK * NM + i] = dk * invN;
-                    tc[TAB_INVK * NM + i] = inv;
-                }
-    }
-    cudaError_t e;
-    if (p->f64) {
-        e = cudaMemcpy(p->ws + p->off_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && p->n_tabc)
-            e = cudaMemcpy(p->ws + p->off_tabc, tabc.data(), size_t(p->n_tabc) * sizeof(cd), cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> t32(tab.begin(), tab.end());
-        e = cudaMemcpy(p->ws + p->off_tab, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && p->n_tabc) {
-            std::vector<float> c32(size_t(p->n_tabc) * 2);
-            for (int64_t i = 0; i < p->n_tabc; ++i) { c32[2 * i] = float(tabc[i].real()); c32[2 * i + 1] = float(tabc[i].imag()); }
-            e = cudaMemcpy(p->ws + p->off_tabc, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice);
-        }
-    }
+    std::vector<char> tab, tabc;
+    table_images(p, c_dt, dx, tab, tabc);
+    cudaError_t e = cudaMemcpy(p->ws + p->off_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->n_tabc)
+        e = cudaMemcpy(p->ws + p->off_tabc, tabc.data(), tabc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(p, e, "copy coefficient tables");
     p->coeffs = true;
     return PSATD_OK;
@@ -593,18 +615,19 @@ static int check_fields(psatd_plan_s* p, const psatd_fields* f, bool need_j) {
     return PSATD_OK;
 }
 
-static LaunchCommon common(psatd_plan_s* p, const psatd_fields* f) {
+// Launch arguments for a workspace image that starts at `base`.
+static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f) {
     LaunchCommon c;
     std::memset(&c, 0, sizeof(c));
-    c.subs = p->ws + p->off_desc;
-    c.segs = p->ws + p->off_seg;
-    c.tw = p->ws + p->off_tw;
-    c.tab = p->ws + p->off_tab;
-    c.tabc = p->ws + p->off_tabc;
-    c.spec = p->ws + p->off_spec;
+    c.subs = base + p->off_desc;
+    c.segs = base + p->off_seg;
+    c.tw = base + p->off_tw;
+    c.tab = base + p->off_tab;
+    c.tabc = base + p->off_tabc;
+    c.spec = base + p->off_spec;
     for (int a = 0; a < 3; ++a) { c.eb[a] = f->E[a]; c.eb[3 + a] = f->B[a]; c.jr[a] = f->J[a]; }
     c.jr[3] = f->rho;
-    c.gauss_part = reinterpret_cast<double*>(p->ws + p->off_gauss);
+    c.gauss_part = reinterpret_cast<double*>(base + p->off_gauss);
     c.nsub = int(p->desc.size());
     c.nseg = int(p->segs.size());
     c.nf = p->nf;
@@ -613,6 +636,8 @@ static LaunchCommon common(psatd_plan_s* p, const psatd_fields* f) {
     for (int i = 0; i < 3; ++i) c.per_sub[i] = p->per_sub[i];
     return c;
 }
+
+static LaunchCommon common(psatd_plan_s* p, const psatd_fields* f) { return common_at(p, p->ws, f); }
 
 static cudaError_t stage(psatd_plan_s* p, int st, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
     return p->f64 ? launch_stage_f64(st, c, i0, n, smem, s) : launch_stage_f32(st, c, i0, n, smem, s);
@@ -629,18 +654,23 @@ int psatd_exchange_guards(psatd_plan_t p, const psatd_fields* f, void* stream) {
     return PSATD_OK;
 }
 
+static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaStream_t s, void* const* ev);
+
 static int push_impl(psatd_plan_s* p, const psatd_fields* f, double* gauss_dev, void* stream, void* const* ev) {
     if (!p) return PSATD_E_ARG;
     if (!p->ws || !p->coeffs) return fail(p, PSATD_E_STATE, "workspace and coefficients must be set before psatd_push");
     int r = check_fields(p, f, true);
     if (r) return r;
     if (gauss_dev && !p->diag) return fail(p, PSATD_E_ARG, "gauss output needs PSATD_GAUSS_DIAG");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return launch_push(p, common(p, f), gauss_dev, static_cast<cudaStream_t>(stream), ev);
+}
+
+// Enqueue every stage of one push (and the Gauss reduction) on stream s.
+static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaStream_t s, void* const* ev) {
     auto mark = [&](int i) -> cudaError_t {
         if (!ev || !ev[i]) return cudaSuccess;
         return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), s);
     };
-    LaunchCommon c = common(p, f);
     cudaError_t e = cudaSuccess;
     if ((e = mark(0)) != cudaSuccess) return cuda_fail(p, e, "event record");
     if (!p->plain) {
@@ -682,3 +712,47 @@ int psatd_destroy(psatd_plan_t p) {
 }
 
 }  // extern "C"
+
+namespace psatd {
+
+// psatd_push on a workspace image at `base` (cap bytes) that the library owns
+// instead of the caller: descriptors, segments, twiddles and tables for
+// (c_dt, dx) are copied there on stream s (stream-ordered, from host images
+// kept in the plan) before the stages are enqueued on the same stream.
+int push_into(psatd_plan_s* p, char* base, size_t cap, double c_dt, const double dx[3], const psatd_fields* f,
+              double* gauss_dev, cudaStream_t s) {
+    if (!p) return PSATD_E_ARG;
+    if (!base) return fail(p, PSATD_E_CUDA, "static workspace address unavailable");
+    if (!dx || !(c_dt == c_dt) || !(dx[0] > 0 && dx[1] > 0 && dx[2] > 0)) return fail(p, PSATD_E_ARG, "bad c_dt or dx");
+    if (p->ws_need > cap)
+        return fail(p, PSATD_E_NOMEM, "plan needs " + std::to_string(p->ws_need) + " bytes of workspace, the static workspace holds " +
+                                          std::to_string(cap));
+    int r = check_fields(p, f, true);
+    if (r) return r;
+    if (gauss_dev && !p->diag) return fail(p, PSATD_E_ARG, "gauss output needs PSATD_GAUSS_DIAG");
+    if (!p->img_valid || p->img_c_dt != c_dt || p->img_dx[0] != dx[0] || p->img_dx[1] != dx[1] || p->img_dx[2] != dx[2]) {
+        p->img_tw = twiddle_image(p);
+        table_images(p, c_dt, dx, p->img_tab, p->img_tabc);
+        p->img_c_dt = c_dt;
+        for (int a = 0; a < 3; ++a) p->img_dx[a] = dx[a];
+        p->img_valid = true;
+    }
+    struct Part { size_t off; const void* src; size_t n; } parts[] = {
+        {p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size()},
+        {p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size()},
+        {p->off_tw, p->img_tw.data(), p->img_tw.size()},
+        {p->off_tab, p->img_tab.data(), p->img_tab.size()},
+        {p->off_tabc, p->img_tabc.data(), p->n_tabc ? p->img_tabc.size() : 0},
+    };
+    for (const Part& q : parts) {
+        if (!q.n) continue;
+        cudaError_t e = cudaMemcpyAsync(base + q.off, q.src, q.n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "copy plan image to the static workspace");
+    }
+    return launch_push(p, common_at(p, base, f), gauss_dev, s, nullptr);
+}
+
+// Record a message on the plan from outside this file.
+int set_error(psatd_plan_s* p, int code, const char* msg) { return fail(p, code, msg); }
+
+}  // namespace psatd

@@ -30,7 +30,9 @@ STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NO
 EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
-           "psatd_push_profiled", "psatd_plan_create_tuned")
+           "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static")
+
+STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 
 class PsatdError(RuntimeError):
@@ -74,6 +76,8 @@ def lib() -> ctypes.CDLL:
         L.psatd_set_coeffs.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
         L.psatd_push.argtypes = [P, ctypes.POINTER(FieldsT), VP, VP]
         L.psatd_push_profiled.argtypes = [P, ctypes.POINTER(FieldsT), VP, VP, ctypes.POINTER(VP)]
+        L.psatd_push_static.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(FieldsT),
+                                         VP, VP]
         L.psatd_exchange_guards.argtypes = [P, ctypes.POINTER(FieldsT), VP]
         L.psatd_destroy.argtypes = [P]
         L.psatd_status_string.argtypes = [ctypes.c_int]
@@ -155,6 +159,15 @@ def psatd_push_profiled(plan, fields: FieldsT, gauss_ptr, stream, events):
     ev = (ctypes.c_void_p * 4)(*[e or None for e in events])
     _check(lib().psatd_push_profiled(plan, ctypes.byref(fields), ctypes.c_void_p(gauss_ptr or 0),
                                      ctypes.c_void_p(stream or 0), ev), plan)
+
+
+def psatd_push_static(plan, c_dt: float, dx: Sequence[float], fields: FieldsT, gauss_ptr: Optional[int] = None,
+                      stream: Optional[int] = None):
+    """The push on the library's static device workspace (no allocation by
+    the caller or the library; see include/psatd.h)."""
+    d = (ctypes.c_double * 3)(*dx)
+    _check(lib().psatd_push_static(plan, c_dt, d, ctypes.byref(fields), ctypes.c_void_p(gauss_ptr or 0),
+                                   ctypes.c_void_p(stream or 0)), plan)
 
 
 def psatd_exchange_guards(plan, fields: FieldsT, stream: Optional[int] = None):
