@@ -8,6 +8,37 @@ constexpr int kMaxDft = 16;       // largest register DFT
 constexpr int kThreads = 256;     // threads per CTA of every stage kernel
 constexpr int kSegSmem = 64;      // exchange segments staged in shared memory per CTA
 
+// Default split n = f1 * f2 of an FFT length (both factors in 1..16): the
+// most balanced pair, then the larger f1; 0 if none exists.
+constexpr int split_first(int n) {
+    int best = -1, f1 = 0;
+    for (int a = 1; a <= kMaxDft; ++a) {
+        if (n % a) continue;
+        const int b = n / a;
+        if (b > kMaxDft) continue;
+        const int score = (a < b ? a : b) * 64 + a;
+        if (score > best) { best = score; f1 = a; }
+    }
+    return best >= 0 ? f1 : 0;
+}
+
+// Field stride of a pass-B chunk in shared memory (complex elements of csz
+// bytes): at least lz*m and padded so that consecutive fields fall on
+// different banks.
+constexpr int pad_field_stride(int lz, int m, int csz) {
+    int fs = lz * m;
+    while ((fs * csz) % 128 != (m * csz) % 128) ++fs;
+    return fs;
+}
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// Cubic local boxes (side L, ng guards, pass-B chunk M, default splits) that
+// have kernels compiled with their geometry fixed at compile time.
+struct FixedGeo { int L, ng, M; };
+constexpr FixedGeo kFixedF32[4] = {{96, 16, 8}, {64, 16, 8}, {48, 8, 8}, {32, 0, 8}};
+constexpr FixedGeo kFixedF64[3] = {{96, 16, 4}, {48, 8, 4}, {32, 0, 4}};
+
 // One local FFT axis of length n = f1 * f2, done as two register stages.
 // Forward output (and inverse input) is in "position" order: frequency
 // k1 + f1*k2 sits at position k1*f2 + k2.
@@ -61,6 +92,7 @@ struct LaunchCommon {
     void* eb[6]; const void* jr[4]; double* gauss_part;
     int nsub, nseg, nf, staggered, own_only;
     int64_t per_sub[3];   // items per subdomain of passes A, B, C when every subdomain has the same shape, else 0
+    int variant;          // index into kFixedF32 / kFixedF64, or -1 for the descriptor-driven kernels
 };
 
 // Coefficient table component order (each Lz*q long, position order).

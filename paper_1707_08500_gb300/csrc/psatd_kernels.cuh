@@ -1,3 +1,4 @@
+#pragma once
 // CUDA kernels of the local-FFT PSATD push for sm_103a.
 //
 // One step of one padded subdomain (Sec. 3.2 of arXiv:1707.08500) is split
@@ -282,18 +283,44 @@ __device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
     return f < 6 ? a.eb[f] : a.jr[f - 6];
 }
 
+// ---- transform geometry ------------------------------------------------------
+// Everything a stage needs to know about one subdomain's local box: read from
+// its descriptor (GeoDyn) or fixed at compile time for a cubic box of side L
+// with NG guards (GeoFix), in which case every stride, loop bound and DFT size
+// below is a constant.
+struct GeoDyn {
+    int Lx, Ly, Lz, h, lxh, pitch, q, ng, nvy, nvz, M, lgM, fs;
+    AxisPlan ax, ay, az;
+    __device__ explicit GeoDyn(const SubDesc& d)
+        : Lx(d.L[0]), Ly(d.L[1]), Lz(d.L[2]), h(d.L[0] >> 1), lxh(d.lxh), pitch(d.pitch), q(d.q), ng(d.ng),
+          nvy(d.nv[1]), nvz(d.nv[2]), M(d.chunkB), lgM(d.lgB), fs(d.fsB), ax(d.ax), ay(d.ay), az(d.az) {}
+};
+
+template <int L, int NG, int MB, int CSZ>
+struct GeoFix {
+    static constexpr int Lx = L, Ly = L, Lz = L, h = L / 2, lxh = L / 2 + 1, pitch = (L / 2 + 1) | 1;
+    static constexpr int q = L * (L / 2 + 1), ng = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
+    static constexpr int M = MB, lgM = ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
+    AxisPlan ax, ay, az;
+    __device__ explicit GeoFix(const SubDesc& d)
+        : ax{h, split_first(h), h / split_first(h), d.ax.tw},
+          ay{L, split_first(L), L / split_first(L), d.ay.tw},
+          az{L, split_first(L), L / split_first(L), d.az.tw} {}
+};
+
 // ---- pass A: x (real) and y forward transforms of one plane ---------------
-template <typename T>
+template <typename T, class G>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
         decode_item<0>(a, it, &d);
-        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
+        const G g(d);
+        const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
         const int loc = int(it - d.itemA);
         const int f = loc / Lz, z = loc - (loc / Lz) * Lz;
-        const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
+        const int h = g.h, pitch = g.pitch, lxh = g.lxh;
         const T* src = field_in(a, f) + d.field_off + int64_t(z) * Ly * Lx;
         // packed complex z[m] = x[2m] + i x[2m+1], row y at y*pitch
         loop2(h, Ly, [&](int y, int m) {
@@ -302,11 +329,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Arg
         cp_async_wait_all();
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
-        fft_fwd<false>(sm, d.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
+        fft_fwd<false>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
         // split the packed transform into the half spectrum X[0..h], walking
         // the pairs (k, h-k) directly in position order (see split_pair)
         const twd<T>* wp = a.tw + d.tw_post;
-        const int f2x = d.ax.f2;
+        const int f2x = g.ax.f2;
         loop2(Ly, split_pairs(h, f2x), [&](int i, int y) {
             cpx<T>* p = sm + y * pitch;
             if (i == 0) {
@@ -327,8 +354,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Arg
         });
         __syncthreads();
         // y: complex FFT of length Ly over the lxh columns
-        fft_fwd<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
-        cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
+        fft_fwd<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
+        cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * g.q;
         loop2(lxh, Ly, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
         __syncthreads();
     }
@@ -349,7 +376,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-template <typename T>
+template <typename T, class G>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
@@ -357,12 +384,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
     __shared__ double red[2][kThreads / 32];
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
         decode_item<1>(a, it, &d);
-        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
-        const int M = d.chunkB, lgM = d.lgB, Q = d.q, lxh = d.lxh;
+        const G g(d);
+        const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
+        const int M = g.M, lgM = g.lgM, Q = g.q, lxh = g.lxh;
         const int q0 = int(it - d.itemB) * M;
         const int mc = min(M, Q - q0);
         const int nf = a.nf;
-        const int fs = d.fsB;                          // padded field stride in shared memory
+        const int fs = g.fs;                           // padded field stride in shared memory
         cpx<T>* spec = a.spec + d.spec_off;
         for (int f = 0; f < nf; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
@@ -385,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
         }
         cp_async_wait_all();
         __syncthreads();
-        fft_fwd<true>(sm, d.az, Batch{nf * M, 1, lgM, fs, M}, a.tw);
+        fft_fwd<true>(sm, g.az, Batch{nf * M, 1, lgM, fs, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
         const T* __restrict__ tk = a.tab + d.tab_k;
@@ -447,8 +475,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
             p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
         });
         __syncthreads();
-        fft_inv<true>(sm, d.az, Batch{6 * M, 1, lgM, fs, M}, a.tw);
-        const int ng = d.ng, nz = d.nv[2];
+        fft_inv<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M}, a.tw);
+        const int ng = g.ng, nz = g.nvz;
         for (int f = 0; f < 6; ++f) {
             cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng) * Q + q0;
             const cpx<T>* s = sm + f * fs + ng * M;
@@ -469,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
 }
 
 // ---- pass C: inverse y and x transforms, fused guard replacement ------------
-template <typename T>
+template <typename T, class G>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
@@ -477,12 +505,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
     __shared__ Segment segs[kSegSmem];
     for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
         decode_item<2>(a, it, &d);
-        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
-        const int nz = d.nv[2], ny = d.nv[1], ng = d.ng;
+        const G g(d);
+        const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
+        const int nz = g.nvz, ny = g.nvy, ng = g.ng;
         const int loc = int(it - d.itemC);
         const int f = loc / nz, z = ng + (loc - (loc / nz) * nz);
-        const int h = Lx >> 1, pitch = d.pitch, lxh = d.lxh;
-        const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q;
+        const int h = g.h, pitch = g.pitch, lxh = g.lxh;
+        const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * g.q;
         loop2(lxh, Ly, [&](int y, int c) { cp_async_c(sm + y * pitch + c, src + y * lxh + c); });
         // this subdomain's exchange segments (the first kSegSmem of them)
         const int nsg = min(d.seg_end - d.seg_begin, kSegSmem);
@@ -493,10 +522,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
         }
         cp_async_wait_all();
         __syncthreads();
-        fft_inv<false>(sm, d.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
+        fft_inv<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
         const twd<T>* wp = a.tw + d.tw_post;
-        const int f2x = d.ax.f2;
+        const int f2x = g.ax.f2;
         cpx<T>* rows = sm + ng * pitch;
         loop2(ny, split_pairs(h, f2x), [&](int i, int y) {
             cpx<T>* p = rows + y * pitch;
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Arg
             }
         });
         __syncthreads();
-        fft_inv<false>(rows, d.ax, Batch{ny, pitch, 0, 0, 1}, a.tw);
+        fft_inv<false>(rows, g.ax, Batch{ny, pitch, 0, 0, 1}, a.tw);
         // store the valid cells of this plane to every box that holds them
         T* out = a.eb[f];
         const T* rp = reinterpret_cast<const T*>(sm);
@@ -561,7 +590,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
 }
 
 // ---- per-subdomain reduction of the Gauss partial sums ----------------------
-__global__ void k_gauss_reduce(const SubDesc* __restrict__ subs, int nsub, const double* __restrict__ part,
+static __global__ void k_gauss_reduce(const SubDesc* __restrict__ subs, int nsub, const double* __restrict__ part,
                                double* __restrict__ out) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int l = threadIdx.x & 31;
@@ -578,8 +607,8 @@ __global__ void k_gauss_reduce(const SubDesc* __restrict__ subs, int nsub, const
     if (l == 0) { out[2 * w] = s1; out[2 * w + 1] = s2; }
 }
 
-// ---- launchers ---------------------------------------------------------------
 
+// ---- launch helpers shared by the per-precision instantiation files ----------
 template <typename T>
 static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     Args<T> a;
@@ -603,50 +632,29 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     return a;
 }
 
-static unsigned grid_for(int64_t n) { return unsigned(n < 2147483647 ? n : 2147483647); }
+static inline unsigned grid_for(int64_t n) { return unsigned(n < 2147483647 ? n : 2147483647); }
 
-template <typename T>
-static cudaError_t set_smem_attr(const void* fn, int bytes) {
+static inline cudaError_t set_smem_attr(const void* fn, int bytes) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-template <typename T>
-cudaError_t launch_stage(int stage, const LaunchCommon& c, int64_t item0, int64_t nitems, int smem, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    Args<T> a = make_args<T>(c, item0, nitems);
-    const void* fn = stage == 0 ? (const void*)k_pass_a<T> : stage == 1 ? (const void*)k_pass_b<T>
-                   : stage == 2 ? (const void*)k_pass_c<T> : (const void*)k_exchange<T>;
-    cudaError_t e = set_smem_attr<T>(fn, smem);
+// Launch pass A, B or C with geometry G (stage 0, 1, 2) or the exchange (3).
+template <typename T, class G>
+static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_t st) {
+    const unsigned grid = grid_for(a.nitems);
+    const void* fn = stage == 0 ? (const void*)k_pass_a<T, G> : stage == 1 ? (const void*)k_pass_b<T, G>
+                   : stage == 2 ? (const void*)k_pass_c<T, G> : (const void*)k_exchange<T>;
+    cudaError_t e = set_smem_attr(fn, smem);
     if (e != cudaSuccess) return e;
     switch (stage) {
-        case 0: k_pass_a<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
-        case 1: k_pass_b<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
-        case 2: k_pass_c<T><<<grid_for(nitems), kThreads, smem, st>>>(a); break;
-        default: k_exchange<T><<<grid_for(nitems), kThreads, 0, st>>>(a); break;
+        case 0: k_pass_a<T, G><<<grid, kThreads, smem, st>>>(a); break;
+        case 1: k_pass_b<T, G><<<grid, kThreads, smem, st>>>(a); break;
+        case 2: k_pass_c<T, G><<<grid, kThreads, smem, st>>>(a); break;
+        default: k_exchange<T><<<grid, kThreads, 0, st>>>(a); break;
     }
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_gauss_reduce(const void* subs, int nsub, const double* part, double* out, cudaStream_t st) {
-    const int threads = 256;
-    const int blocks = (nsub * 32 + threads - 1) / threads;
-    k_gauss_reduce<<<blocks, threads, 0, st>>>(static_cast<const SubDesc*>(subs), nsub, part, out);
-    return cudaPeekAtLastError();
-}
-
-template cudaError_t launch_stage<float>(int, const LaunchCommon&, int64_t, int64_t, int, cudaStream_t);
-template cudaError_t launch_stage<double>(int, const LaunchCommon&, int64_t, int64_t, int, cudaStream_t);
-
-}  // namespace psatd
-
-// entry points used by the host plan code (C++ linkage inside the library)
-namespace psatd {
-cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
-    return launch_stage<float>(stage, c, i0, n, smem, s);
-}
-cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s) {
-    return launch_stage<double>(stage, c, i0, n, smem, s);
-}
 }  // namespace psatd

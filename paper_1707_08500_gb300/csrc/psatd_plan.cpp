@@ -97,16 +97,10 @@ double kmod(int i, int L, double du, int p, bool stag) {
 }
 
 bool factor(int n, int& f1, int& f2) {
-    // prefer the most balanced split with both factors in 1..16
-    int best = -1;
-    for (int a = 1; a <= kMaxDft; ++a) {
-        if (n % a) continue;
-        int b = n / a;
-        if (b > kMaxDft) continue;
-        int score = std::min(a, b) * 64 + a;   // balanced first, then larger f1
-        if (score > best) { best = score; f1 = a; f2 = b; }
-    }
-    return best >= 0;
+    f1 = split_first(n);   // the most balanced split with both factors in 1..16
+    if (!f1) return false;
+    f2 = n / f1;
+    return true;
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -135,6 +129,7 @@ struct psatd_plan_s {
     int64_t items[3] = {0, 0, 0};
     int64_t exch_items = 0;
     int64_t per_sub[3] = {0, 0, 0};   // items per subdomain when uniform
+    int variant = -1;                  // compile-time geometry variant, or -1
     int smemA = 0, smemB = 0, smemC = 0;
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_spec = 0, ws_need = 0;
@@ -468,6 +463,23 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         }
     }
     p->spec_elems = p->plain ? maxspec : spec;
+    // kernels with compile-time geometry apply when every subdomain is the
+    // same cubic box with the default splits and chunk width
+    {
+        const FixedGeo* list = p->f64 ? kFixedF64 : kFixedF32;
+        const int nl = p->f64 ? int(sizeof(kFixedF64) / sizeof(FixedGeo)) : int(sizeof(kFixedF32) / sizeof(FixedGeo));
+        for (int v = 0; v < nl && p->variant < 0; ++v) {
+            const int L = list[v].L, g = list[v].ng, M = list[v].M;
+            bool ok = true;
+            for (const SubDesc& d : p->desc) {
+                ok = ok && d.L[0] == L && d.L[1] == L && d.L[2] == L && d.ng == g && d.nv[0] == L - 2 * g &&
+                     d.nv[1] == L - 2 * g && d.nv[2] == L - 2 * g && d.chunkB == M && d.ax.f1 == split_first(L / 2) &&
+                     d.ay.f1 == split_first(L) && d.az.f1 == split_first(L) && d.fsB == pad_field_stride(L, M, csz) &&
+                     d.pitch == ((L / 2 + 1) | 1);
+            }
+            if (ok) p->variant = v;
+        }
+    }
     if (std::max(p->smemA, p->smemB) > 227 * 1024)
         return bad(PSATD_E_UNSUPPORTED, "a local plane does not fit in shared memory");
     // --- exchange segments (source valid box -> destination local box) ----------
@@ -557,6 +569,12 @@ int psatd_workspace_bytes(psatd_plan_t p, size_t* b) {
     return PSATD_OK;
 }
 
+int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
+    if (!p || !v) return PSATD_E_ARG;
+    *v = p->variant;
+    return PSATD_OK;
+}
+
 int psatd_push_launches(psatd_plan_t p, int32_t* n) {
     if (!p || !n) return PSATD_E_ARG;
     int nsub = int(p->desc.size());
@@ -634,6 +652,7 @@ static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f
     c.staggered = p->stag ? 1 : 0;
     c.own_only = 0;
     for (int i = 0; i < 3; ++i) c.per_sub[i] = p->per_sub[i];
+    c.variant = p->variant;
     return c;
 }
 

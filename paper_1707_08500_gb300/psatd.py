@@ -30,7 +30,7 @@ STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NO
 EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
-           "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static")
+           "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         L.psatd_last_error.argtypes = [P]
         L.psatd_last_error.restype = ctypes.c_char_p
         L.psatd_push_launches.argtypes = [P, ctypes.POINTER(I32)]
+        L.psatd_geometry_variant.argtypes = [P, ctypes.POINTER(I32)]
         for name in EXPORTS:
             if name not in ("psatd_status_string", "psatd_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -189,6 +190,12 @@ def psatd_last_error(plan) -> str:
 def psatd_push_launches(plan) -> int:
     n = ctypes.c_int32()
     _check(lib().psatd_push_launches(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def psatd_geometry_variant(plan) -> int:
+    n = ctypes.c_int32()
+    _check(lib().psatd_geometry_variant(plan, ctypes.byref(n)), plan)
     return n.value
 
 

@@ -129,3 +129,20 @@ def test_exchange_segments_cover_every_local_cell_once(P):
     h = P.psatd_plan_create(g, subs, P.PSATD_F32)
     assert P.psatd_layout(h, 0)[1] == (28, 36, 36)
     P.psatd_destroy(h)
+
+
+def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
+    cases = [("mirror1024", P.PSATD_F32, 0), ("broadband256", P.PSATD_F32, 0), ("mirror1024", P.PSATD_F64, 0),
+             ("yee64", P.PSATD_F64 | P.PSATD_STAGGERED, 1), ("plain32", P.PSATD_F64, 2), ("uneven48", P.PSATD_F32, -1)]
+    for name, flags, want in cases:
+        wl = I.workload(name)
+        h = P.psatd_plan_create(wl.global_n, wl.subs, flags)
+        try:
+            assert P.psatd_geometry_variant(h) == want, name
+        finally:
+            P.psatd_destroy(h)
+    # a non-default split falls back to the descriptor-driven kernels
+    wl = I.workload("broadband256")
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 8, "f1": [4, 0, 0]})
+    assert P.psatd_geometry_variant(h) == -1
+    P.psatd_destroy(h)
