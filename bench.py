@@ -106,14 +106,25 @@ def stage_bytes(wl, nf: int, esz: int):
     return {"A": A, "B": B, "C": C}, local
 
 
+KERNEL_SOURCES = ("psatd_kernels.cuh", "psatd_kernels_f32.cu", "small_dft.cuh", "psatd_internal.h")
+
+
+def kernels_sha256() -> str:
+    """Hash of the stage-kernel sources (the profile summaries record it)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1707_08500_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_mirror1024.json")) as f:
             t = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1707_08500_gb300", "csrc", "psatd_kernels.cu"), "rb").read()
-        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+        if t.get("kernels_sha256") != kernels_sha256():
             return None
         return t["bytes_per_launch"].get(kernel)
     except Exception:
@@ -167,7 +178,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     wl = I.workload(args.workload)
     gauss = not args.no_gauss
-    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev)
+    tuning = {"chunk_b": args.chunk_b, "f1": [0, 0, 0]} if args.chunk_b else None
+    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev, tuning=tuning)
     fill_solver(sol, wl, dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -234,6 +246,7 @@ def run_ours(args, rank, world, local_rank):
                           "three_pass_bytes_per_step": sum(by.values()),
                           "frac_three_pass": round(sum(by.values()) / (ms_step / 1e3) / 1e9 / peak, 4)},
         "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
+        "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan), "tuning": tuning},
         "clocks": clk.summary(),
     }
     # ---- end to end through the C ABI with per-step host copies ----------------
@@ -351,6 +364,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-subs", type=int, default=2)
+    ap.add_argument("--chunk-b", type=int, default=0, help="pass-B chunk width (0 = plan default)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -36,7 +36,7 @@ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 // Cubic local boxes (side L, ng guards, pass-B chunk M, default splits) that
 // have kernels compiled with their geometry fixed at compile time.
 struct FixedGeo { int L, ng, M; };
-constexpr FixedGeo kFixedF32[4] = {{96, 16, 8}, {64, 16, 8}, {48, 8, 8}, {32, 0, 8}};
+constexpr FixedGeo kFixedF32[5] = {{96, 16, 8}, {64, 16, 8}, {48, 8, 8}, {32, 0, 8}, {96, 16, 4}};
 constexpr FixedGeo kFixedF64[3] = {{96, 16, 4}, {48, 8, 4}, {32, 0, 4}};
 
 // One local FFT axis of length n = f1 * f2, done as two register stages.

@@ -27,6 +27,18 @@
 #include "psatd_internal.h"
 #include "small_dft.cuh"
 
+// Minimum resident CTAs per SM requested from the compiler for each stage
+// kernel (FP32; FP64 uses 2), which caps its registers per thread.
+#ifndef PSATD_MINB_A
+#define PSATD_MINB_A 5
+#endif
+#ifndef PSATD_MINB_B
+#define PSATD_MINB_B 3
+#endif
+#ifndef PSATD_MINB_C
+#define PSATD_MINB_C 5
+#endif
+
 namespace psatd {
 
 // A table twiddle as an FP32 hi + lo pair (lo = 0 in FP64).
@@ -310,7 +322,7 @@ struct GeoFix {
 
 // ---- pass A: x (real) and y forward transforms of one plane ---------------
 template <typename T, class G>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_a(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k_pass_a(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
@@ -377,7 +389,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 template <typename T, class G>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k_pass_b(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
@@ -498,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_pass_b(Arg
 
 // ---- pass C: inverse y and x transforms, fused guard replacement ------------
 template <typename T, class G>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_pass_c(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k_pass_c(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
