@@ -178,8 +178,17 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     wl = I.workload(args.workload)
     gauss = not args.no_gauss
-    tuning = {"chunk_b": args.chunk_b, "f1": [0, 0, 0]} if args.chunk_b else None
-    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev, tuning=tuning)
+    flags = P.PSATD_F32 | (P.PSATD_GAUSS_DIAG if gauss else 0)
+    if args.chunk_b:
+        tuning = {"chunk_b": args.chunk_b, "f1": [0, 0, 0]}
+    elif args.tune:
+        from paper_1707_08500_gb300 import tune as T
+        tuning = T.autotune(wl, flags, device=dev)
+        torch.cuda.empty_cache()
+    else:
+        tuning = None
+    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev, tuning=tuning,
+                   extra_flags=P.PSATD_GRID_PER_ITEM if args.grid_per_item else 0)
     fill_solver(sol, wl, dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -195,18 +204,41 @@ def run_ours(args, rank, world, local_rank):
     evs = [[mkev() for _ in range(4)] for _ in range(args.steps)]
     t0, t1 = mkev(), mkev()
     torch.cuda.synchronize()
+    gp = sol.gauss_out.data_ptr() if gauss else None
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
         t0.record(stream)
         for k in range(args.steps):
-            P.psatd_push_profiled(sol.plan, sol.fields, sol.gauss_out.data_ptr() if gauss else None, sp,
-                                  [e.cuda_event for e in evs[k]])
+            P.psatd_push_profiled(sol.plan, sol.fields, gp, sp, [e.cuda_event for e in evs[k]])
         t1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    graph_ms = None
+    if not args.no_graph:
+        # the same K steps captured as one CUDA graph and replayed (the stage
+        # events above cannot be timed inside a graph, so this is reported beside)
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                cs = torch.cuda.current_stream(dev).cuda_stream
+                for k in range(args.steps):
+                    P.psatd_push(sol.plan, sol.fields, gp, cs)
+            graph.replay()
+            torch.cuda.synchronize()
+            g0, g1 = mkev(), mkev()
+            torch.cuda.synchronize()
+            g0.record(stream)
+            graph.replay()
+            g1.record(stream)
+            torch.cuda.synchronize()
+            graph_ms = g0.elapsed_time(g1) / args.steps
+            del graph
+        except Exception as exc:
+            print(f"graph capture unavailable: {exc}", file=sys.stderr)
+            torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     stage_ms = {st: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
                 for i, st in enumerate("ABC")}
@@ -246,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
                           "three_pass_bytes_per_step": sum(by.values()),
                           "frac_three_pass": round(sum(by.values()) / (ms_step / 1e3) / 1e9 / peak, 4)},
         "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
-        "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan), "tuning": tuning},
+        "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan), "tuning": tuning,
+                    "persistent": not args.grid_per_item, "cuda_graph_ms_per_step": None if graph_ms is None else round(graph_ms, 4)},
         "clocks": clk.summary(),
     }
     # ---- end to end through the C ABI with per-step host copies ----------------
@@ -365,6 +398,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-subs", type=int, default=2)
     ap.add_argument("--chunk-b", type=int, default=0, help="pass-B chunk width (0 = plan default)")
+    ap.add_argument("--tune", action="store_true", help="autotune launch shapes before timing")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
+    ap.add_argument("--grid-per-item", action="store_true", help="one CTA per work item instead of persistent grids")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

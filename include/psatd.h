@@ -61,6 +61,10 @@ extern "C" {
                                      kernel (default: all subdomains batched in
                                      one launch per stage, guard images written
                                      by the inverse-FFT stage itself)            */
+#define PSATD_GRID_PER_ITEM  0x20 /* launch one CTA per work item instead of the
+                                     default persistent grid (as many CTAs as
+                                     fit on the GPU, drawing work items from a
+                                     counter in the workspace)                   */
 
 /* One subdomain.  Its valid cells are the global indices [lo, lo+n) per axis
  * (x, y, z); its local (padded) box is [lo-ng, lo+n+ng), of extent

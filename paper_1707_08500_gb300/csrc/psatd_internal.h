@@ -90,6 +90,8 @@ struct Segment {
 struct LaunchCommon {
     const void* subs; const void* segs; const void* tw; const void* tab; const void* tabc; void* spec;
     void* eb[6]; const void* jr[4]; double* gauss_part;
+    unsigned long long* work;   // persistent-launch work counter (in the workspace)
+    int persistent;             // 1: persistent grids drawing tickets; 0: one CTA per work item
     int nsub, nseg, nf, staggered, own_only;
     int64_t per_sub[3];   // items per subdomain of passes A, B, C when every subdomain has the same shape, else 0
     int variant;          // index into kFixedF32 / kFixedF64, or -1 for the descriptor-driven kernels

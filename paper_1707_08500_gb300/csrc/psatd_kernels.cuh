@@ -79,6 +79,8 @@ struct Args {
     T* eb[6];               // Ex Ey Ez Bx By Bz
     const T* jr[4];         // Jx Jy Jz rho
     double* gauss_part;     // 2 per pass-B item
+    unsigned long long* work;   // work-item ticket counter of this launch (zeroed before it)
+    int persistent;         // 1: CTAs draw items from `work`; 0: CTA b does item item0 + b
     int64_t item0, nitems;  // items handled by this launch
     int64_t per_sub[3];     // items per subdomain of each stage when uniform, else 0
     int nsub, nseg;
@@ -295,6 +297,29 @@ __device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
     return f < 6 ? a.eb[f] : a.jr[f - 6];
 }
 
+// Work loop of the stage kernels.  Persistent launches: each CTA draws the
+// next unprocessed item of the launch from a global ticket counter (zeroed by
+// the host before the launch) until every item is taken; the ticket for the
+// following item is drawn at the start of the current one, into the other of
+// two shared slots, so no CTA waits on the atomic between items.  Otherwise
+// CTA b processes item item0 + b only.  Every loop body ends with
+// __syncthreads(), which orders the slot writes and reads.
+template <typename T>
+struct Tickets {
+    const Args<T>& a;
+    int64_t* slot;
+    int par = 0;
+    __device__ Tickets(const Args<T>& args, int64_t* s) : a(args), slot(s) {
+        if (threadIdx.x == 0) slot[0] = a.persistent ? int64_t(atomicAdd(a.work, 1ull)) : int64_t(blockIdx.x);
+        __syncthreads();
+    }
+    __device__ int64_t current() const { const int64_t k = slot[par]; return k < a.nitems ? a.item0 + k : -1; }
+    __device__ void prefetch() {
+        if (threadIdx.x == 0) slot[par ^ 1] = a.persistent ? int64_t(atomicAdd(a.work, 1ull)) : a.nitems;
+    }
+    __device__ void advance() { par ^= 1; }
+};
+
 // ---- transform geometry ------------------------------------------------------
 // Everything a stage needs to know about one subdomain's local box: read from
 // its descriptor (GeoDyn) or fixed at compile time for a cubic box of side L
@@ -326,7 +351,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
-    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
         decode_item<0>(a, it, &d);
         const G g(d);
         const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
@@ -394,7 +422,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
     __shared__ double red[2][kThreads / 32];
-    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
         decode_item<1>(a, it, &d);
         const G g(d);
         const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
@@ -515,7 +546,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
     __shared__ Segment segs[kSegSmem];
-    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
         decode_item<2>(a, it, &d);
         const G g(d);
         const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
@@ -583,7 +617,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
 // ---- standalone guard exchange ---------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
-    for (int64_t it = a.item0 + blockIdx.x; it < a.item0 + a.nitems; it += gridDim.x) {
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
         int lo = 0, hi = a.nseg - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -598,6 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
             T* dst = fld + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
             loop2(sg.ex, sg.ey, [&](int yy, int xx) { dst[int64_t(yy) * sg.dLx + xx] = src[int64_t(yy) * sd.L[0] + xx]; });
         }
+        __syncthreads();
     }
 }
 
@@ -633,6 +671,8 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     for (int i = 0; i < 6; ++i) a.eb[i] = static_cast<T*>(c.eb[i]);
     for (int i = 0; i < 4; ++i) a.jr[i] = static_cast<const T*>(c.jr[i]);
     a.gauss_part = c.gauss_part;
+    a.work = c.work;
+    a.persistent = c.persistent;
     a.item0 = item0;
     for (int i = 0; i < 3; ++i) a.per_sub[i] = c.per_sub[i];
     a.nitems = nitems;
@@ -655,11 +695,22 @@ static inline cudaError_t set_smem_attr(const void* fn, int bytes) {
 // Launch pass A, B or C with geometry G (stage 0, 1, 2) or the exchange (3).
 template <typename T, class G>
 static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_t st) {
-    const unsigned grid = grid_for(a.nitems);
     const void* fn = stage == 0 ? (const void*)k_pass_a<T, G> : stage == 1 ? (const void*)k_pass_b<T, G>
                    : stage == 2 ? (const void*)k_pass_c<T, G> : (const void*)k_exchange<T>;
     cudaError_t e = set_smem_attr(fn, smem);
     if (e != cudaSuccess) return e;
+    unsigned grid = grid_for(a.nitems);
+    if (a.persistent) {
+        // one persistent launch: as many CTAs as can be resident, each drawing
+        // work items from the ticket counter
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int64_t resident = int64_t(per_sm > 0 ? per_sm : 1) * nsm;
+        grid = grid_for(a.nitems < resident ? a.nitems : resident);
+        if ((e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    }
     switch (stage) {
         case 0: k_pass_a<T, G><<<grid, kThreads, smem, st>>>(a); break;
         case 1: k_pass_b<T, G><<<grid, kThreads, smem, st>>>(a); break;

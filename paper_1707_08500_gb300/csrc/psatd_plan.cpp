@@ -132,7 +132,7 @@ struct psatd_plan_s {
     int variant = -1;                  // compile-time geometry variant, or -1
     int smemA = 0, smemB = 0, smemC = 0;
     // workspace layout (bytes)
-    size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_spec = 0, ws_need = 0;
+    size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_work = 0, off_spec = 0, ws_need = 0;
     int64_t spec_elems = 0;
     char* ws = nullptr;
     size_t ws_size = 0;
@@ -300,7 +300,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     auto bad = [&](int code, const std::string& m) { int c = fail(p, code, m); delete p; return c; };
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
-    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN))
+    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -543,6 +543,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     p->off_tab = o; o = align_up(o + size_t(p->n_tab) * esz, 256);
     p->off_tabc = o; o = align_up(o + size_t(std::max<int64_t>(p->n_tabc, 1)) * 2 * esz, 256);
     p->off_gauss = o; o = align_up(o + size_t(std::max<int64_t>(p->items[1], 1)) * 2 * sizeof(double), 256);
+    p->off_work = o; o = align_up(o + 8 * sizeof(unsigned long long), 256);
     p->off_spec = o; o = align_up(o + size_t(p->spec_elems) * 2 * esz, 256);
     p->ws_need = o;
     *out = p;
@@ -646,6 +647,8 @@ static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f
     for (int a = 0; a < 3; ++a) { c.eb[a] = f->E[a]; c.eb[3 + a] = f->B[a]; c.jr[a] = f->J[a]; }
     c.jr[3] = f->rho;
     c.gauss_part = reinterpret_cast<double*>(base + p->off_gauss);
+    c.work = reinterpret_cast<unsigned long long*>(base + p->off_work);
+    c.persistent = (p->flags & PSATD_GRID_PER_ITEM) ? 0 : 1;
     c.nsub = int(p->desc.size());
     c.nseg = int(p->segs.size());
     c.nf = p->nf;

@@ -23,6 +23,7 @@ PSATD_F64 = 0x02
 PSATD_STAGGERED = 0x04
 PSATD_GAUSS_DIAG = 0x08
 PSATD_PLAIN = 0x10
+PSATD_GRID_PER_ITEM = 0x20
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}
@@ -217,7 +218,7 @@ class Solver:
     at ``layout[s][0]`` as a dense [Lz][Ly][Lx] box."""
 
     def __init__(self, wl: "_inputs.Workload", precision: Optional[str] = None, plain: bool = False,
-                 gauss: bool = False, device="cuda", tuning: Optional[dict] = None):
+                 gauss: bool = False, device="cuda", tuning: Optional[dict] = None, extra_flags: int = 0):
         self.wl = wl
         self.precision = precision or wl.precision
         self.dtype = torch.float64 if self.precision == "f64" else torch.float32
@@ -228,6 +229,7 @@ class Solver:
             flags |= PSATD_GAUSS_DIAG
         if plain:
             flags |= PSATD_PLAIN
+        flags |= extra_flags
         self.flags = flags
         self.gauss = gauss
         self.device = torch.device(device)
