@@ -103,7 +103,7 @@ def _check(code: int, plan=None):
 # ---- thin wrappers with the C names -------------------------------------------
 def psatd_plan_create(global_n: Sequence[int], subs: Sequence, flags: int, tuning: Optional[dict] = None) -> ctypes.c_void_p:
     """tuning: None or {"chunk_b": M, "f1": (fx, fy, fz)} (0 = default)."""
-    arr = (SubT * len(subs))()
+    arr = (SubT * max(len(subs), 1))()
     for i, s in enumerate(subs):
         arr[i].lo[:] = list(s.lo)
         arr[i].n[:] = list(s.n)

@@ -67,7 +67,8 @@ def test_plain_schedule_launch_count(P):
 
 @pytest.mark.parametrize("case,code", [
     ("overlap", -2), ("gap", -2), ("outside", -2), ("odd_order", -2),
-    ("odd_local_x", -5), ("big_prime", -5), ("no_precision", -1), ("both_precisions", -1),
+    ("odd_local_x", -5), ("big_prime", -5), ("no_precision", -1), ("both_precisions", -1), ("no_subdomains", -1),
+    ("unknown_flag", -1), ("negative_guard", -2),
 ])
 def test_plan_rejects_bad_input(P, case, code):
     g = (32, 32, 32)
@@ -91,6 +92,12 @@ def test_plan_rejects_bad_input(P, case, code):
         flags = 0
     elif case == "both_precisions":
         flags = P.PSATD_F32 | P.PSATD_F64
+    elif case == "no_subdomains":
+        subs = []
+    elif case == "unknown_flag":
+        flags = P.PSATD_F32 | 0x400
+    elif case == "negative_guard":
+        subs = [I.Sub(s.lo, s.n, -1, 8) for s in subs]
     with pytest.raises(P.PsatdError) as e:
         P.psatd_plan_create(g, subs, flags)
     assert e.value.code == code

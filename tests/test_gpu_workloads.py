@@ -1,0 +1,176 @@
+"""The five workloads at full size through the C ABI, against the FP64 oracle.
+
+Configurations the oracle finishes in seconds run complete trajectories
+(plain32: 100 FP64 steps; yee64: 200 FP64 steps).  The large FP32 workloads
+run in the launch configuration bench.py times (batched, persistent grids,
+fixed-geometry kernels where they apply) and are checked after one step on
+every subdomain (uneven48) or on sampled subdomains computed one by one by
+the oracle (broadband256, mirror1024), including the guard images that the
+fused exchange wrote into the sampled boxes.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import psatd_oracle as O
+from paper_1707_08500_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_08500_gb300 import build
+    build.build()
+    from paper_1707_08500_gb300 import psatd
+    return psatd
+
+
+def _np(d):
+    return {k: v.numpy() for k, v in d.items()}
+
+
+def _solver(P, wl, glob=None, **kw):
+    sol = P.Solver(wl, **kw)
+    if glob is not None:
+        sol.load_global(glob, names=I.EB_NAMES, guards=False)
+        sol.load_global(glob, names=("Jx", "Jy", "Jz", "rho"), guards=True)
+        sol.exchange()
+    return sol
+
+
+def test_plain32_100_steps_f64(P):
+    wl = I.workload("plain32")
+    glob = I.global_fields(wl)
+    sol = _solver(P, wl, glob)
+    assert P.psatd_geometry_variant(sol.plan) == 2
+    for _ in range(wl.steps):
+        sol.push()
+    torch.cuda.synchronize()
+    ref = O.run(_np(glob), wl, wl.steps)
+    err = O.rel_l2(_np(sol.gather_global()), ref)
+    print(f"plain32 FP64 after {wl.steps} steps: rel L2 {err:.3e}")
+    assert err < 1e-12
+
+
+def test_yee64_200_steps_f64(P):
+    wl = I.workload("yee64")
+    glob = I.global_fields(wl)
+    sol = _solver(P, wl, glob)
+    for _ in range(wl.steps):
+        sol.push()
+    torch.cuda.synchronize()
+    g = _np(glob)
+    ref = O.run(g, wl, wl.steps)
+    got = _np(sol.gather_global())
+    err = O.rel_l2(got, ref)
+    # the local solution differs from the global-FFT one by the guard
+    # truncation, whose size is not fixed by the paper (reported only)
+    gl = dict(g)
+    for _ in range(wl.steps):
+        gl = dict(gl, **O.global_push(gl, 32, wl.dx, wl.c_dt, True))
+    trunc = O.rel_l2(ref, gl)
+    print(f"yee64 FP64 after {wl.steps} steps: GPU vs local oracle {err:.3e}; local vs global {trunc:.3e}")
+    assert err < 1e-12
+
+
+def test_uneven48_one_step_f32_all_subdomains(P):
+    wl = I.workload("uneven48")
+    glob = I.global_fields(wl)
+    sol = _solver(P, wl, glob, gauss=True)
+    assert P.psatd_geometry_variant(sol.plan) == -1
+    sol.push()
+    torch.cuda.synchronize()
+    gs = []
+    ref = O.step(_np(glob), wl, gauss_out=gs)
+    err = O.rel_l2(_np(sol.gather_global()), ref)
+    print(f"uneven48 FP32 one step: rel L2 {err:.3e}")
+    assert err < 2e-6
+    np.testing.assert_allclose(sol.gauss_sums()[:, 1], np.array(gs)[:, 1], rtol=1e-3, atol=1e-6)
+
+
+def _sampled_check(P, wl, samples, tol):
+    """One batched FP32 step on the full workload; every cell of the sampled
+    subdomains' padded boxes (valid cells and the guard images written by the
+    fused exchange) against the oracle's push of the subdomain that owns it.
+
+    An FP32 transform rounds relative to the magnitude of the whole box it
+    transforms, and the laser/slab fields span many decades inside one box, so
+    the cells owned by subdomain t are compared with an error normalised by
+    the norm of t's whole pushed padded box."""
+    dev = torch.device("cuda")
+    sol = P.Solver(wl, gauss=True)
+    glob = None
+    if wl.fields == "laser_slab":
+        for s, sd in enumerate(wl.subs):
+            b = I.box_fields(wl, sd, device=dev)
+            for n in I.FIELD_NAMES:
+                sol.box(n, s).copy_(b[n])
+    else:
+        glob = I.global_fields(wl)
+        sol.load_global(glob)
+        glob = _np(glob)
+
+    def box_of(td):
+        if glob is None:
+            return {k: v.numpy() for k, v in I.box_fields(wl, td, device="cpu").items()}
+        return {k: O.extract_box(v, td.lo, td.local, td.ng) for k, v in glob.items()}
+    sol.push()
+    torch.cuda.synchronize()
+    assert P.psatd_geometry_variant(sol.plan) == 0
+    for s in samples:
+        sd = wl.subs[s]
+        lo = [sd.lo[a] - sd.ng for a in range(3)]
+        gidx = [(np.arange(sd.local[a]) + lo[a]) % wl.global_n[a] for a in range(3)]
+        got = {n: sol.box(n, s).double().cpu().numpy() for n in I.EB_NAMES}
+        covered = np.zeros(sd.local[::-1], dtype=bool)
+        worst = 0.0
+        for t, td in enumerate(wl.subs):
+            inx = [np.nonzero((gidx[a] >= td.lo[a]) & (gidx[a] < td.lo[a] + td.n[a]))[0] for a in range(3)]
+            if any(len(v) == 0 for v in inx):
+                continue
+            out, _ = O.local_push(box_of(td), td.local, wl.dx, td.p, wl.c_dt, wl.staggered)
+            sel = np.ix_(inx[2], inx[1], inx[0])
+            src = np.ix_(gidx[2][inx[2]] - td.lo[2] + td.ng, gidx[1][inx[1]] - td.lo[1] + td.ng,
+                         gidx[0][inx[0]] - td.lo[0] + td.ng)
+            num = sum(float(((got[n][sel] - out[n][src]) ** 2).sum()) for n in I.EB_NAMES)
+            den = sum(float((out[n] ** 2).sum()) for n in I.EB_NAMES)
+            worst = max(worst, (num / max(den, 1e-300)) ** 0.5)
+            covered[sel] = True
+        assert covered.all()
+        print(f"{wl.name} subdomain {s}: worst owner-normalised rel L2 over its padded box {worst:.3e}")
+        assert worst < tol, (s, worst)
+
+
+def test_broadband256_one_step_sampled(P):
+    wl = I.workload("broadband256")
+    _sampled_check(P, wl, samples=[0, 21, 63], tol=2e-6)
+
+
+def test_mirror1024_one_step_sampled(P):
+    """The bench workload: subdomains in the laser, in the slab and at the
+    periodic corner."""
+    wl = I.workload("mirror1024")
+    laser = next(s for s, sd in enumerate(wl.subs) if sd.lo == (256, 192, 192))
+    slab = next(s for s, sd in enumerate(wl.subs) if sd.lo == (640, 256, 256))
+    _sampled_check(P, wl, samples=[0, laser, slab], tol=2e-6)
+
+
+@pytest.mark.parametrize("case", ["thin", "long_axis", "smallest"])
+def test_degenerate_shapes_f64(P, case):
+    if case == "thin":          # a 2-cell-wide subdomain with guards wider than it
+        wl = I.custom("thin", (20, 12, 12), ((2, 18), (12,), (12,)), 3, 6, fields="wavepacket", precision="f64")
+    elif case == "long_axis":   # the longest supported local length (16 x 16) on x
+        wl = I.custom("long", (256, 8, 8), ((256,), (8,), (8,)), 0, 16, fields="wavepacket", precision="f64")
+    else:                       # the smallest local box
+        wl = I.custom("small", (4, 4, 4), ((4,), (4,), (4,)), 0, 2, fields="wavepacket", precision="f64")
+    glob = I.global_fields(wl)
+    sol = _solver(P, wl, glob)
+    for _ in range(3):
+        sol.push()
+    torch.cuda.synchronize()
+    ref = O.run(_np(glob), wl, 3)
+    err = O.rel_l2(_np(sol.gather_global()), ref)
+    assert err < 1e-12, err
