@@ -26,6 +26,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "Gcell-steps/s of local-FFT PSATD push, batched FP32 vs plain FP64; % HBM roof"
+
 
 def _peaks():
     try:
@@ -87,6 +89,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over all ranks (timing only; no data-path collective)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(valid_cells: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling):
+    valid cells of all ranks per second, in Gcell-steps/s."""
+    return valid_cells * world / (ms_per_step / 1e3) / 1e9
+
+
 def stage_bytes(wl, nf: int, esz: int):
     """Algorithmic HBM bytes per launch of each stage (unique inputs + outputs):
     A reads nf real fields and writes nf half spectra; B reads nf spectra and
@@ -178,16 +197,19 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     wl = I.workload(args.workload)
     gauss = not args.no_gauss
-    flags = P.PSATD_F32 | (P.PSATD_GAUSS_DIAG if gauss else 0)
+    prec = args.precision or ("f32" if wl.precision == "f32" else "f64")
+    flags = (P.PSATD_F32 if prec == "f32" else P.PSATD_F64) | (P.PSATD_GAUSS_DIAG if gauss else 0)
+    if wl.staggered:
+        flags |= P.PSATD_STAGGERED
     if args.chunk_b:
         tuning = {"chunk_b": args.chunk_b, "f1": [0, 0, 0]}
-    elif args.tune:
+    elif not args.no_tune:
         from paper_1707_08500_gb300 import tune as T
         tuning = T.autotune(wl, flags, device=dev)
         torch.cuda.empty_cache()
     else:
         tuning = None
-    sol = P.Solver(wl, precision="f32", gauss=gauss, device=dev, tuning=tuning,
+    sol = P.Solver(wl, precision=prec, gauss=gauss, device=dev, tuning=tuning,
                    extra_flags=P.PSATD_GRID_PER_ITEM if args.grid_per_item else 0)
     fill_solver(sol, wl, dev)
     stream = torch.cuda.current_stream(dev)
@@ -242,27 +264,24 @@ def run_ours(args, rank, world, local_rank):
     ms = t0.elapsed_time(t1)
     stage_ms = {st: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
                 for i, st in enumerate("ABC")}
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_step = ms / args.steps
     valid = wl.valid_cells
-    value = valid * world / (ms_step / 1e3) / 1e9
+    value = replica_value(valid, world, ms_step)
     nf = 10 if gauss else 9
-    by, local = stage_bytes(wl, nf, 4)
+    by, local = stage_bytes(wl, nf, 4 if prec == "f32" else 8)
     peak, peak_kind = _peaks()
     dom = max(stage_ms, key=stage_ms.get)
     names = {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"}
     stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
                    "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
     achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
-    fused_bytes = (64 if gauss else 60) * local
+    fused_bytes = (16 if gauss else 15) * (4 if prec == "f32" else 8) * local
     result = {
-        "metric": "Gcell-steps/s of local-FFT PSATD push (valid cells x steps / s), batched FP32; % HBM roof",
+        "metric": METRIC,
         "value": round(value, 4), "unit": "Gcell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
         "config": {"workload": wl.name, "global_n": list(wl.global_n), "subdomains": len(wl.subs),
                    "local_n": list(wl.subs[0].local), "guards": wl.subs[0].ng, "order": wl.subs[0].p,
                    "c_dt": wl.c_dt, "gauss_diag": gauss, "valid_cells": valid, "local_cells": local,
@@ -302,11 +321,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / ksteps
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        result["e2e"] = {"value": round(valid * world / (ems / 1e3) / 1e9, 4), "unit": "Gcell-steps/s",
+        ems = max_over_ranks(ems, world, dev)
+        result["e2e"] = {"value": round(replica_value(valid, world, ems), 4), "unit": "Gcell-steps/s",
                          "h2d_bytes_per_step": sum(h.numel() * 4 for h in host.values()),
                          "d2h_bytes_per_step": gh.numel() * 8 if gauss else 0, "steps": ksteps,
                          "ms_per_step": round(ems, 3),
@@ -345,6 +361,27 @@ def run_ours(args, rank, world, local_rank):
                                "launches_per_step": P.psatd_push_launches(s64.plan)}
         del s64, s32
         torch.cuda.empty_cache()
+    # ---- FP32 batched vs FP64 plain over S steps (reported accuracy) -----------
+    if args.accuracy_steps and rank == 0:
+        torch.cuda.empty_cache()
+        a32 = P.Solver(wl, precision="f32", gauss=False, device=dev, tuning=tuning)
+        fill_solver(a32, wl, dev)
+        for _ in range(args.accuracy_steps):
+            a32.push(sp)
+        torch.cuda.synchronize()
+        keep = {n: a32.arenas[n].clone() for n in I.EB_NAMES}
+        del a32
+        torch.cuda.empty_cache()
+        a64 = P.Solver(wl, precision="f64", plain=True, gauss=False, device=dev)
+        fill_solver(a64, wl, dev)
+        for _ in range(args.accuracy_steps):
+            a64.push(sp)
+        torch.cuda.synchronize()
+        num = sum(float(((keep[n].double() - a64.arenas[n]) ** 2).sum()) for n in I.EB_NAMES)
+        den = sum(float((a64.arenas[n] ** 2).sum()) for n in I.EB_NAMES)
+        result["accuracy"] = {"steps": args.accuracy_steps, "f32_batched_vs_f64_plain_rel_l2": float(f"{math.sqrt(num / den):.3e}")}
+        del a64, keep
+        torch.cuda.empty_cache()
     # ---- CPU oracle baseline (rank 0, N = 1 only) -------------------------------
     if not args.skip_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_budget)
@@ -374,7 +411,7 @@ def run_reference(args, rank, world):
     cells = sum(sd.n[0] * sd.n[1] * sd.n[2] for sd, _ in boxes)
     v = cells / dt / 1e9
     sample = f"each step = {len(boxes)} of {len(wl.subs)} subdomain pushes ({cells} valid cells)"
-    return {"impl": "reference", "metric": "Gcell-steps/s of local-FFT PSATD push (valid cells x steps / s), batched FP32; % HBM roof",
+    return {"impl": "reference", "metric": METRIC,
             "value": round(v, 6), "unit": "Gcell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -398,9 +435,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-subs", type=int, default=2)
     ap.add_argument("--chunk-b", type=int, default=0, help="pass-B chunk width (0 = plan default)")
-    ap.add_argument("--tune", action="store_true", help="autotune launch shapes before timing")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (plan default shapes)")
+    ap.add_argument("--precision", choices=["f32", "f64"], default=None, help="default: the workload's")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--grid-per-item", action="store_true", help="one CTA per work item instead of persistent grids")
+    ap.add_argument("--accuracy-steps", type=int, default=0, help="also report FP32 batched vs FP64 plain after S steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
