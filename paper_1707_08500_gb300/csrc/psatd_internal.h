@@ -66,8 +66,8 @@ struct SubDesc {
     int64_t tab_ph;      // complex offset of stagger phases (same layout), or -1
     int seg_begin, seg_end;     // exchange segments whose source is this subdomain
     int64_t itemA, itemB, itemC; // first work item of this subdomain in each stage
-    int chunkB;          // modes per pass-B chunk (M, a power of two)
-    int lgB;             // log2(M)
+    int chunkB;          // modes per pass-B chunk (M)
+    int lgB;             // log2(M) when M is a power of two, else -1
     int fsB;             // padded stride between fields of a pass-B chunk in shared memory
     int pad1;
 };

@@ -33,7 +33,7 @@
 #define PSATD_MINB_A 5
 #endif
 #ifndef PSATD_MINB_B
-#define PSATD_MINB_B 3
+#define PSATD_MINB_B 4
 #endif
 #ifndef PSATD_MINB_C
 #define PSATD_MINB_C 5
@@ -147,20 +147,27 @@ __device__ __forceinline__ void cp_async_c(cpx<T>* dst, const cpx<T>* src) {
 }
 
 // Batched transforms in shared memory.  Transform b starts at b*s_in
-// (single-level) or (b mod 2^lg)*s_in + (b >> lg)*s_out (two-level, used for
-// several fields of one pencil chunk); its elements are es apart.
+// (single-level) or (b mod inner)*s_in + (b / inner)*s_out (two-level, used
+// for several fields of one pencil chunk; lg = log2(inner) when inner is a
+// power of two, else -1); its elements are es apart.
 struct Batch {
     int count;   // number of transforms
     int s_in;
-    int lg;      // log2 of transforms per group (two-level batches only)
+    int lg;
     int s_out;
     int es;
+    int inner;
 };
 
 template <bool TWO>
 __device__ __forceinline__ int boff(const Batch& b, int i) {
-    if constexpr (TWO) return (i & ((1 << b.lg) - 1)) * b.s_in + (i >> b.lg) * b.s_out;
-    else return i * b.s_in;
+    if constexpr (TWO) {
+        if (b.lg >= 0) return (i & ((1 << b.lg) - 1)) * b.s_in + (i >> b.lg) * b.s_out;
+        const int o = i / b.inner;
+        return (i - o * b.inner) * b.s_in + o * b.s_out;
+    } else {
+        return i * b.s_in;
+    }
 }
 
 // Visit every (outer, inner) pair with inner in [0, count), outer in
@@ -337,7 +344,7 @@ template <int L, int NG, int MB, int CSZ>
 struct GeoFix {
     static constexpr int Lx = L, Ly = L, Lz = L, h = L / 2, lxh = L / 2 + 1, pitch = (L / 2 + 1) | 1;
     static constexpr int q = L * (L / 2 + 1), ng = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
-    static constexpr int M = MB, lgM = ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
+    static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
     AxisPlan ax, ay, az;
     __device__ explicit GeoFix(const SubDesc& d)
         : ax{h, split_first(h), h / split_first(h), d.ax.tw},
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k
         cp_async_wait_all();
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
-        fft_fwd<false>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1}, a.tw);
+        fft_fwd<false>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1, 1}, a.tw);
         // split the packed transform into the half spectrum X[0..h], walking
         // the pairs (k, h-k) directly in position order (see split_pair)
         const twd<T>* wp = a.tw + d.tw_post;
@@ -394,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k
         });
         __syncthreads();
         // y: complex FFT of length Ly over the lxh columns
-        fft_fwd<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
+        fft_fwd<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
         cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * g.q;
         loop2(lxh, Ly, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
         __syncthreads();
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         }
         cp_async_wait_all();
         __syncthreads();
-        fft_fwd<true>(sm, g.az, Batch{nf * M, 1, lgM, fs, M}, a.tw);
+        fft_fwd<true>(sm, g.az, Batch{nf * M, 1, lgM, fs, M, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
         const T* __restrict__ tk = a.tab + d.tab_k;
@@ -518,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
             p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
         });
         __syncthreads();
-        fft_inv<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M}, a.tw);
+        fft_inv<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
         const int ng = g.ng, nz = g.nvz;
         for (int f = 0; f < 6; ++f) {
             cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng) * Q + q0;
@@ -568,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
         }
         cp_async_wait_all();
         __syncthreads();
-        fft_inv<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch}, a.tw);
+        fft_inv<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
         const twd<T>* wp = a.tw + d.tw_post;
         const int f2x = g.ax.f2;
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
             }
         });
         __syncthreads();
-        fft_inv<false>(rows, g.ax, Batch{ny, pitch, 0, 0, 1}, a.tw);
+        fft_inv<false>(rows, g.ax, Batch{ny, pitch, 0, 0, 1, 1}, a.tw);
         // store the valid cells of this plane to every box that holds them
         T* out = a.eb[f];
         const T* rp = reinterpret_cast<const T*>(sm);

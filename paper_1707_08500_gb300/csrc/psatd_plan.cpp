@@ -291,7 +291,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     if (!out || !global_n || !subs || nsub <= 0) return PSATD_E_ARG;
     if (tuning) {
         const int cb = tuning->chunk_b;
-        if (cb < 0 || cb > 64 || (cb & (cb - 1))) return PSATD_E_ARG;
+        if (cb < 0 || cb > 64) return PSATD_E_ARG;
         for (int a = 0; a < 3; ++a) if (tuning->f1[a] < 0 || tuning->f1[a] > kMaxDft) return PSATD_E_ARG;
     }
     *out = nullptr;
@@ -434,6 +434,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         d.chunkB = M;
         d.lgB = 0;
         while ((1 << d.lgB) < M) ++d.lgB;
+        if ((1 << d.lgB) != M) d.lgB = -1;
         // field stride padded so that consecutive fields of a chunk fall on
         // different shared-memory banks
         int fs = d.L[2] * M;
