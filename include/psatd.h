@@ -61,6 +61,10 @@ extern "C" {
                                      kernel (default: all subdomains batched in
                                      one launch per stage, guard images written
                                      by the inverse-FFT stage itself)            */
+#define PSATD_2D             0x40 /* a two-dimensional (x, y) problem: global_n[2]
+                                     == 1, every subdomain has n[2] == 1, and
+                                     there are no guard cells along z (the
+                                     local boxes are Lx x Ly x 1)                */
 #define PSATD_GRID_PER_ITEM  0x20 /* launch one CTA per work item instead of the
                                      default persistent grid (as many CTAs as
                                      fit on the GPU, drawing work items from a

@@ -274,14 +274,25 @@ def local_push(fields: Dict[str, np.ndarray], L, dx, p: int, c_dt: float, stagge
 # ---------------------------------------------------------------------------
 # decomposition, guard extraction and exchange (Sec. 3.2, Fig. 3)
 # ---------------------------------------------------------------------------
+def _guards(ng):
+    """Guard widths (x, y, z) from an int or a 3-tuple."""
+    return tuple(ng) if isinstance(ng, (tuple, list)) else (ng, ng, ng)
+
+
+def sub_guards(sd):
+    """Guard widths (x, y, z) of a subdomain (none along z in 2D problems)."""
+    return tuple(getattr(sd, "guards", (sd.ng, sd.ng, sd.ng)))
+
+
 def extract_box(G: np.ndarray, lo, L, ng) -> np.ndarray:
     """Padded box of a subdomain read from the periodic global array by global
     index modulo the grid (this is also the guard exchange: every local cell
-    holds the owner's valid value)."""
+    holds the owner's valid value).  ng: guard width, or (gx, gy, gz)."""
     Nz, Ny, Nx = G.shape
-    ix = (np.arange(L[0]) + lo[0] - ng) % Nx
-    iy = (np.arange(L[1]) + lo[1] - ng) % Ny
-    iz = (np.arange(L[2]) + lo[2] - ng) % Nz
+    gx, gy, gz = _guards(ng)
+    ix = (np.arange(L[0]) + lo[0] - gx) % Nx
+    iy = (np.arange(L[1]) + lo[1] - gy) % Ny
+    iz = (np.arange(L[2]) + lo[2] - gz) % Nz
     return G[np.ix_(iz, iy, ix)]
 
 
@@ -307,13 +318,14 @@ def step(glob: Dict[str, np.ndarray], wl, gauss_out: List | None = None) -> Dict
     new = {n: np.empty_like(glob[n]) for n in EB}
     for sd in wl.subs:
         L = sd.local
-        loc = {n: extract_box(glob[n], sd.lo, L, sd.ng) for n in glob}
+        gx, gy, gz = sub_guards(sd)
+        loc = {n: extract_box(glob[n], sd.lo, L, (gx, gy, gz)) for n in glob}
         out, gauss = local_push(loc, L, wl.dx, sd.p, wl.c_dt, wl.staggered)
         if gauss_out is not None:
             gauss_out.append(gauss)
-        (x0, y0, z0), (nx, ny, nz), g = sd.lo, sd.n, sd.ng
+        (x0, y0, z0), (nx, ny, nz) = sd.lo, sd.n
         for n in EB:
-            new[n][z0:z0 + nz, y0:y0 + ny, x0:x0 + nx] = out[n][g:g + nz, g:g + ny, g:g + nx]
+            new[n][z0:z0 + nz, y0:y0 + ny, x0:x0 + nx] = out[n][gz:gz + nz, gy:gy + ny, gx:gx + nx]
     for n in glob:
         if n not in new:
             new[n] = glob[n]
@@ -328,7 +340,7 @@ def run(glob: Dict[str, np.ndarray], wl, steps: int) -> Dict[str, np.ndarray]:
 
 def local_arena(glob: Dict[str, np.ndarray], wl, name: str) -> List[np.ndarray]:
     """Padded boxes of every subdomain for one field (guards from the owners)."""
-    return [extract_box(glob[name], sd.lo, sd.local, sd.ng) for sd in wl.subs]
+    return [extract_box(glob[name], sd.lo, sd.local, sub_guards(sd)) for sd in wl.subs]
 
 
 def global_push(glob: Dict[str, np.ndarray], p: int, dx, c_dt: float, staggered: bool):

@@ -51,7 +51,7 @@ struct AxisPlan {
 struct SubDesc {
     int L[3];            // local extents x, y, z
     int nv[3];           // valid extents
-    int ng;
+    int ng;              // guard cells per side along x and y
     int lxh;             // Lx/2 + 1 (half-spectrum columns)
     int pitch;           // complex row pitch of a plane in shared memory (odd)
     int q;               // Ly * lxh: modes per z plane
@@ -66,6 +66,7 @@ struct SubDesc {
     int64_t tab_ph;      // complex offset of stagger phases (same layout), or -1
     int seg_begin, seg_end;     // exchange segments whose source is this subdomain
     int64_t itemA, itemB, itemC; // first work item of this subdomain in each stage
+    int ngz;             // guard cells per side along z (0 for 2D problems)
     int chunkB;          // modes per pass-B chunk (M)
     int lgB;             // log2(M) when M is a power of two, else -1
     int fsB;             // padded stride between fields of a pass-B chunk in shared memory

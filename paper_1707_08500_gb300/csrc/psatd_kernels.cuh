@@ -333,17 +333,17 @@ struct Tickets {
 // with NG guards (GeoFix), in which case every stride, loop bound and DFT size
 // below is a constant.
 struct GeoDyn {
-    int Lx, Ly, Lz, h, lxh, pitch, q, ng, nvy, nvz, M, lgM, fs;
+    int Lx, Ly, Lz, h, lxh, pitch, q, ng, ngz, nvy, nvz, M, lgM, fs;
     AxisPlan ax, ay, az;
     __device__ explicit GeoDyn(const SubDesc& d)
-        : Lx(d.L[0]), Ly(d.L[1]), Lz(d.L[2]), h(d.L[0] >> 1), lxh(d.lxh), pitch(d.pitch), q(d.q), ng(d.ng),
+        : Lx(d.L[0]), Ly(d.L[1]), Lz(d.L[2]), h(d.L[0] >> 1), lxh(d.lxh), pitch(d.pitch), q(d.q), ng(d.ng), ngz(d.ngz),
           nvy(d.nv[1]), nvz(d.nv[2]), M(d.chunkB), lgM(d.lgB), fs(d.fsB), ax(d.ax), ay(d.ay), az(d.az) {}
 };
 
 template <int L, int NG, int MB, int CSZ>
 struct GeoFix {
     static constexpr int Lx = L, Ly = L, Lz = L, h = L / 2, lxh = L / 2 + 1, pitch = (L / 2 + 1) | 1;
-    static constexpr int q = L * (L / 2 + 1), ng = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
+    static constexpr int q = L * (L / 2 + 1), ng = NG, ngz = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
     static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
     AxisPlan ax, ay, az;
     __device__ explicit GeoFix(const SubDesc& d)
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         });
         __syncthreads();
         fft_inv<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
-        const int ng = g.ng, nz = g.nvz;
+        const int ng = g.ngz, nz = g.nvz;
         for (int f = 0; f < 6; ++f) {
             cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng) * Q + q0;
             const cpx<T>* s = sm + f * fs + ng * M;
@@ -561,8 +561,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
         const G g(d);
         const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
         const int nz = g.nvz, ny = g.nvy, ng = g.ng;
+        const int ngz = g.ngz;
         const int loc = int(it - d.itemC);
-        const int f = loc / nz, z = ng + (loc - (loc / nz) * nz);
+        const int f = loc / nz, z = ngz + (loc - (loc / nz) * nz);
         const int h = g.h, pitch = g.pitch, lxh = g.lxh;
         const cpx<T>* src = a.spec + d.spec_off + int64_t(f * Lz + z) * g.q;
         loop2(lxh, Ly, [&](int y, int c) { cp_async_c(sm + y * pitch + c, src + y * lxh + c); });

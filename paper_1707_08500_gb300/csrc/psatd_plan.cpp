@@ -300,7 +300,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     auto bad = [&](int code, const std::string& m) { int c = fail(p, code, m); delete p; return c; };
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
-    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM))
+    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -312,6 +312,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         if (global_n[a] <= 0) return bad(PSATD_E_SHAPE, "global extents must be positive");
         p->gn[a] = global_n[a];
     }
+    const bool two_d = flags & PSATD_2D;
+    if (two_d && global_n[2] != 1) return bad(PSATD_E_SHAPE, "PSATD_2D needs global_n[2] == 1");
     p->subs.assign(subs, subs + nsub);
     // --- tiling: inside the grid, disjoint, volumes add up -------------------
     int64_t vol = 0;
@@ -352,8 +354,10 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         const psatd_sub& u = subs[s];
         SubDesc& d = p->desc[s];
         std::memset(&d, 0, sizeof(d));
-        for (int a = 0; a < 3; ++a) { d.nv[a] = u.n[a]; d.L[a] = u.n[a] + 2 * u.ng; }
+        const int ngz = two_d ? 0 : u.ng;
+        for (int a = 0; a < 3; ++a) { d.nv[a] = u.n[a]; d.L[a] = u.n[a] + 2 * (a == 2 ? ngz : u.ng); }
         d.ng = u.ng;
+        d.ngz = ngz;
         if (d.L[0] % 2 || d.L[0] < 2) return bad(PSATD_E_UNSUPPORTED, "local x length must be even");
         int h = d.L[0] / 2;
         if (!factor(h, d.ax.f1, d.ax.f2) || !factor(d.L[1], d.ay.f1, d.ay.f2) || !factor(d.L[2], d.az.f1, d.az.f2))
@@ -430,6 +434,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
         int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
+        if (!(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 64 modes
+            while (M < 64 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 64 * 1024) M *= 2;
         while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
         d.chunkB = M;
         d.lgB = 0;
@@ -473,7 +479,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
             const int L = list[v].L, g = list[v].ng, M = list[v].M;
             bool ok = true;
             for (const SubDesc& d : p->desc) {
-                ok = ok && d.L[0] == L && d.L[1] == L && d.L[2] == L && d.ng == g && d.nv[0] == L - 2 * g &&
+                ok = ok && d.L[0] == L && d.L[1] == L && d.L[2] == L && d.ng == g && d.ngz == g && d.nv[0] == L - 2 * g &&
                      d.nv[1] == L - 2 * g && d.nv[2] == L - 2 * g && d.chunkB == M && d.ax.f1 == split_first(L / 2) &&
                      d.ay.f1 == split_first(L) && d.az.f1 == split_first(L) && d.fsB == pad_field_stride(L, M, csz) &&
                      d.pitch == ((L / 2 + 1) | 1);
@@ -494,7 +500,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
             std::vector<std::tuple<long, long, long>> ax[3];
             for (int a = 0; a < 3; ++a) {
                 long N = global_n[a];
-                long b0 = long(D.lo[a]) - D.ng, b1 = long(D.lo[a]) + D.n[a] + D.ng;
+                const long gD = (a == 2 && two_d) ? 0 : D.ng;
+                long b0 = long(D.lo[a]) - gD, b1 = long(D.lo[a]) + D.n[a] + gD;
                 long tmin = (long)std::floor(double(b0 - (S.lo[a] + S.n[a])) / N) - 1;
                 long tmax = (long)std::ceil(double(b1 - S.lo[a]) / N) + 1;
                 for (long t = tmin; t <= tmax; ++t) {
@@ -514,8 +521,9 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
                 long hi[3] = {std::get<2>(X), std::get<2>(Y), std::get<2>(Z)};
                 int x0[3], ext[3], off[3];
                 for (int a = 0; a < 3; ++a) {
-                    long src_origin = S.lo[a] + t[a] * global_n[a] - S.ng;   // global coord of source local 0
-                    long dst_origin = long(D.lo[a]) - D.ng;
+                    const long gS = (a == 2 && two_d) ? 0 : S.ng, gD = (a == 2 && two_d) ? 0 : D.ng;
+                    long src_origin = S.lo[a] + t[a] * global_n[a] - gS;   // global coord of source local 0
+                    long dst_origin = long(D.lo[a]) - gD;
                     x0[a] = int(lo[a] - src_origin);
                     ext[a] = int(hi[a] - lo[a]);
                     off[a] = int(src_origin - dst_origin);

@@ -43,15 +43,21 @@ STAGGER = {
 @dataclasses.dataclass(frozen=True)
 class Sub:
     """One subdomain: valid box [lo, lo+n) of the global grid, padded by ng
-    guard cells on every side, solved at stencil order p (0 = infinite)."""
+    guard cells on every side (none along z when zguard is False, as in 2D
+    problems), solved at stencil order p (0 = infinite)."""
     lo: Tuple[int, int, int]
     n: Tuple[int, int, int]
     ng: int
     p: int
+    zguard: bool = True
+
+    @property
+    def guards(self) -> Tuple[int, int, int]:
+        return (self.ng, self.ng, self.ng if self.zguard else 0)
 
     @property
     def local(self) -> Tuple[int, int, int]:
-        return tuple(int(v) + 2 * self.ng for v in self.n)
+        return tuple(int(v) + 2 * g for v, g in zip(self.n, self.guards))
 
 
 @dataclasses.dataclass
@@ -66,6 +72,7 @@ class Workload:
     dx: Tuple[float, float, float] = (1.0, 1.0, 1.0)
     c_dt: float = 0.5
     staggered: bool = False
+    two_d: bool = False
 
     @property
     def valid_cells(self) -> int:
@@ -194,12 +201,16 @@ WORKLOADS = ("plain32", "yee64", "broadband256", "uneven48", "mirror1024")
 
 
 def custom(name, global_n, cuts, ng, p, fields="broadband", steps=1, precision="f32",
-           seed=1707, staggered=False, c_dt=0.5) -> Workload:
-    """A workload with explicit per-axis cuts ((cx...), (cy...), (cz...))."""
+           seed=1707, staggered=False, c_dt=0.5, two_d=False) -> Workload:
+    """A workload with explicit per-axis cuts ((cx...), (cy...), (cz...)).
+    two_d: a 2D (x, y) problem, global_n[2] == 1 and no guards along z."""
     subs = tensor_decomposition(cuts[0], cuts[1], cuts[2], ng, p)
+    if two_d:
+        assert global_n[2] == 1
+        subs = [dataclasses.replace(sd, zguard=False) for sd in subs]
     assert tuple(sum(c) for c in cuts) == tuple(global_n)
     return Workload(name, tuple(global_n), subs, fields, steps, precision, seed,
-                    staggered=staggered, c_dt=c_dt)
+                    staggered=staggered, c_dt=c_dt, two_d=two_d)
 
 
 # ---------------------------------------------------------------------------
@@ -385,7 +396,7 @@ def global_fields(wl: Workload, device="cpu") -> Dict[str, torch.Tensor]:
 def box_fields(wl: Workload, sub: Sub, device="cpu") -> Dict[str, torch.Tensor]:
     """The ten fields on one subdomain's padded box, read from the global field
     by periodic index (used to sample a few subdomains of a large workload)."""
-    lo = tuple(sub.lo[a] - sub.ng for a in range(3))
+    lo = tuple(sub.lo[a] - sub.guards[a] for a in range(3))
     if wl.fields == "laser_slab":
         return laser_slab_box(wl, lo, sub.local, device)
     g = global_fields(wl, device)

@@ -24,6 +24,7 @@ PSATD_STAGGERED = 0x04
 PSATD_GAUSS_DIAG = 0x08
 PSATD_PLAIN = 0x10
 PSATD_GRID_PER_ITEM = 0x20
+PSATD_2D = 0x40
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}
@@ -225,6 +226,8 @@ class Solver:
         flags = PSATD_F64 if self.precision == "f64" else PSATD_F32
         if wl.staggered:
             flags |= PSATD_STAGGERED
+        if wl.two_d:
+            flags |= PSATD_2D
         if gauss:
             flags |= PSATD_GAUSS_DIAG
         if plain:
@@ -273,16 +276,16 @@ class Solver:
             for n in names:
                 g = glob[n].to(self.device)
                 b = self.box(n, s)
+                gx, gy, gz = sd.guards
                 if guards:
-                    ix = (torch.arange(sd.local[0], device=self.device) + sd.lo[0] - sd.ng) % nx
-                    iy = (torch.arange(sd.local[1], device=self.device) + sd.lo[1] - sd.ng) % ny
-                    iz = (torch.arange(sd.local[2], device=self.device) + sd.lo[2] - sd.ng) % nz
+                    ix = (torch.arange(sd.local[0], device=self.device) + sd.lo[0] - gx) % nx
+                    iy = (torch.arange(sd.local[1], device=self.device) + sd.lo[1] - gy) % ny
+                    iz = (torch.arange(sd.local[2], device=self.device) + sd.lo[2] - gz) % nz
                     b.copy_(g[iz][:, iy][:, :, ix].to(self.dtype))
                 else:
                     x0, y0, z0 = sd.lo
                     vx, vy, vz = sd.n
-                    gg = sd.ng
-                    b[gg:gg + vz, gg:gg + vy, gg:gg + vx].copy_(g[z0:z0 + vz, y0:y0 + vy, x0:x0 + vx].to(self.dtype))
+                    b[gz:gz + vz, gy:gy + vy, gx:gx + vx].copy_(g[z0:z0 + vz, y0:y0 + vy, x0:x0 + vx].to(self.dtype))
 
     def load_boxes(self, boxes: Dict[int, Dict[str, torch.Tensor]]):
         for s, fl in boxes.items():
@@ -296,10 +299,10 @@ class Solver:
         for s, sd in enumerate(self.wl.subs):
             x0, y0, z0 = sd.lo
             vx, vy, vz = sd.n
-            g = sd.ng
+            gx, gy, gz = sd.guards
             for n in names:
                 out[n][z0:z0 + vz, y0:y0 + vy, x0:x0 + vx] = \
-                    self.box(n, s)[g:g + vz, g:g + vy, g:g + vx].to("cpu", torch.float64)
+                    self.box(n, s)[gz:gz + vz, gy:gy + vy, gx:gx + vx].to("cpu", torch.float64)
         return out
 
     # -- solver calls --

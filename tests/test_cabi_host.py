@@ -153,3 +153,20 @@ def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
     h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 8, "f1": [4, 0, 0]})
     assert P.psatd_geometry_variant(h) == -1
     P.psatd_destroy(h)
+
+
+def test_two_d_plans(P):
+    """PSATD_2D: one cell along z, no guards along z (the local box is
+    (nx + 2 ng, ny + 2 ng, 1)); a 3D global grid is rejected."""
+    wl = I.custom("p2", (64, 32, 1), ((40, 24), (32,), (1,)), 8, 32, two_d=True)
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32 | P.PSATD_2D)
+    try:
+        assert P.psatd_layout(h, 0)[1] == (56, 48, 1)
+        assert P.psatd_layout(h, 1)[1] == (40, 48, 1)
+        assert P.psatd_geometry_variant(h) == -1
+    finally:
+        P.psatd_destroy(h)
+    subs = I.tensor_decomposition([16, 16], [32], [32], 4, 8)
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_plan_create((32, 32, 32), subs, P.PSATD_F32 | P.PSATD_2D)
+    assert e.value.code == -2

@@ -76,6 +76,15 @@ CASES = {
                                        precision="f32"), 5, 1e-5),
     "wide_guard_f64": (lambda: I.custom("wg", (40, 16, 16), ((8, 32), (16,), (16,)), 10, 6,
                                         fields="wavepacket", precision="f64"), 2, 1e-12),
+    # 2D problems: one cell along z, no guards along z
+    "twod_f64": (lambda: I.custom("2d", (48, 30, 1), ((30, 18), (16, 14), (1,)), 6, 16, fields="wavepacket",
+                                  precision="f64", two_d=True), 3, 1e-12),
+    "twod_stag_f64": (lambda: I.custom("2ds", (40, 36, 1), ((24, 16), (20, 16), (1,)), 4, 8, fields="wavepacket",
+                                       precision="f64", staggered=True, two_d=True), 3, 1e-12),
+    "twod_f32": (lambda: I.custom("2df", (64, 64, 1), ((32, 32), (32, 32), (1,)), 8, 16, fields="broadband",
+                                  precision="f32", two_d=True), 5, 1e-5),
+    "twod_global_f64": (lambda: I.custom("2dg", (128, 96, 1), ((128,), (96,), (1,)), 0, 0, fields="wavepacket",
+                                         precision="f64", two_d=True), 2, 1e-12),
 }
 
 
@@ -93,7 +102,7 @@ def test_push_matches_oracle(P, name, plain):
     # guards hold the owners' values after the step (fused or separate exchange)
     for s in range(len(wl.subs)):
         for n in I.EB_NAMES:
-            exp = O.extract_box(ref[n], wl.subs[s].lo, wl.subs[s].local, wl.subs[s].ng)
+            exp = O.extract_box(ref[n], wl.subs[s].lo, wl.subs[s].local, O.sub_guards(wl.subs[s]))
             box = sol.box(n, s).double().cpu().numpy()
             scale = max(np.abs(exp).max(), 1e-30)
             assert np.abs(box - exp).max() / scale < 50 * tol, (name, s, n)
@@ -112,9 +121,15 @@ def test_exchange_is_exact_copy(P):
             assert np.array_equal(sol.box(n, s).cpu().numpy(), exp), (s, n)
 
 
+def _twod(precision):
+    return I.custom("2dg", (48, 30, 1), ((30, 18), (16, 14), (1,)), 6, 16, fields="wavepacket",
+                    precision=precision, two_d=True)
+
+
+@pytest.mark.parametrize("shape", ["3d", "2d"])
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 1e-3)])
-def test_gauss_partials_match_oracle(P, precision, tol):
-    wl = _mixed(precision)
+def test_gauss_partials_match_oracle(P, precision, tol, shape):
+    wl = _mixed(precision) if shape == "3d" else _twod(precision)
     glob = I.global_fields(wl)
     _, gsum = _run_gpu(P, wl, glob, 2, gauss=True)
     _, osum = _oracle(wl, glob, 2)

@@ -363,3 +363,59 @@ def test_extract_box_periodic_wrap():
     assert box[0, 0, 0] == G[-1, -1, -1]
     assert box[1, 1, 1] == G[0, 0, 0]
     assert box[1, 1, 7] == G[0, 0, 0]   # x wraps twice over a 6-wide axis
+
+
+# --------------------------------------------------------------------------
+# 2D problems (x, y; one cell along z, no guards along z)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("p,staggered", [(0, False), (16, False), (8, True)])
+def test_2d_local_equals_global_when_padded_box_is_one_period(p, staggered):
+    N = 16
+    wl = I.custom("sp2", (N, N, 1), ((8, 8), (8, 8), (1,)), 4, p, staggered=staggered, c_dt=0.45, two_d=True)
+    assert all(sd.local == (N, N, 1) for sd in wl.subs)
+    rng = np.random.default_rng(3)
+    f = {nm: rng.standard_normal((1, N, N)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    a, b = f, f
+    for _ in range(4):
+        a = O.step(a, wl)
+        b = dict(b, **O.global_push(b, p, (1.0,) * 3, 0.45, staggered))
+    assert O.rel_l2(a, b) < 1e-13
+
+
+@pytest.mark.parametrize("p,staggered", [(16, False), (8, True)])
+def test_2d_equals_z_invariant_3d_decomposition(p, staggered):
+    """A 2D problem is the z-invariant special case of the 3D one: with guards
+    along z every z cell of the padded box repeats the one plane, so only
+    kz = 0 is populated and the push must match the guard-free 2D push."""
+    Nx, Ny = 40, 24
+    wl2 = I.custom("a2", (Nx, Ny, 1), ((24, 16), (12, 12), (1,)), 4, p, staggered=staggered, two_d=True)
+    wl3 = I.custom("a3", (Nx, Ny, 1), ((24, 16), (12, 12), (1,)), 4, p, staggered=staggered)
+    assert wl2.subs[0].local == (32, 20, 1) and wl3.subs[0].local == (32, 20, 9)
+    rng = np.random.default_rng(4)
+    f = {nm: rng.standard_normal((1, Ny, Nx)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    assert O.rel_l2(O.run(f, wl2, 3), O.run(f, wl3, 3)) < 1e-13
+
+
+def test_2d_unit_pulse_spurious_signal_stays_in_guards():
+    """Fig. 3 (2D): a unit pulse in the larger of two unequal subdomains;
+    after one push the local solution differs from the global one mostly in
+    the guard cells, and the exchange (step 3) removes it from the valid
+    cells that the global solution fixes up to the truncation."""
+    Nx, Ny, ng, p = 64, 32, 8, 32
+    wl = I.custom("pulse2", (Nx, Ny, 1), ((40, 24), (Ny,), (1,)), ng, p, c_dt=0.5, two_d=True)
+    f = {nm: np.zeros((1, Ny, Nx)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    f["Ez"][0, Ny // 2, 20] = 1.0
+    ref = O.global_push(f, p, (1.0,) * 3, 0.5, False)
+    for sd in wl.subs:
+        gx, gy, gz = O.sub_guards(sd)
+        assert gz == 0
+        loc = {nm: O.extract_box(f[nm], sd.lo, sd.local, (gx, gy, gz)) for nm in f}
+        out, _ = O.local_push(loc, sd.local, (1.0,) * 3, p, 0.5, False)
+        exp = {nm: O.extract_box(ref[nm], sd.lo, sd.local, (gx, gy, gz)) for nm in O.EB}
+        valid = np.zeros(out["Ez"].shape, bool)
+        valid[:, gy:-gy, gx:-gx] = True
+        dv = max(np.abs(out[nm] - exp[nm])[valid].max() for nm in O.EB)
+        dg = max(np.abs(out[nm] - exp[nm])[~valid].max() for nm in O.EB)
+        assert dv < 1e-2 * dg, (dv, dg)
+    # after the exchange the whole step is close to the global push
+    assert O.rel_l2(O.step(f, wl), ref) < 1e-3
