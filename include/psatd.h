@@ -69,6 +69,15 @@ extern "C" {
                                      default persistent grid (as many CTAs as
                                      fit on the GPU, drawing work items from a
                                      counter in the workspace)                   */
+#define PSATD_SPLIT_PLANES   0x80 /* split-plane schedule: the x and y transforms
+                                     of the forward and inverse plane stages run
+                                     as separate row and column launches (five
+                                     stages per push instead of three).  Chosen
+                                     automatically when an (x, y) plane of a
+                                     local box does not fit in shared memory
+                                     (e.g. one box over the whole grid, the
+                                     paper's PSATD-global, Sec. 3.2 / Fig. 2b);
+                                     this flag forces it for any plan         */
 
 /* One subdomain.  Its valid cells are the global indices [lo, lo+n) per axis
  * (x, y, z); its local (padded) box is [lo-ng, lo+n+ng), of extent
@@ -98,10 +107,11 @@ typedef struct psatd_plan_s* psatd_plan_t;
 
 /* Build a plan (host only, no CUDA call).  global_n: periodic global grid
  * (x, y, z).  Validated: the valid boxes tile the global grid exactly; every
- * order is 0 or even; every local length is >= 4, the local x length is even,
- * and every local length factors as n1*n2 with 1 <= n1, n2 <= 16; flags hold
- * exactly one of PSATD_F32 / PSATD_F64.  Guard widths may exceed a
- * neighbour's width (the guard is then filled from several owners). */
+ * order is 0 or even; the local x length is even, and every local length
+ * (half of it along x) factors as n1*n2 with 1 <= n1, n2 <= 16, so local
+ * boxes reach 512 x 256 x 256; flags hold exactly one of PSATD_F32 /
+ * PSATD_F64.  Guard widths may exceed a neighbour's width (the guard is then
+ * filled from several owners). */
 int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
                       const psatd_sub* subs, int32_t nsub, int32_t flags);
 

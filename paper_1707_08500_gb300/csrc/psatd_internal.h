@@ -7,6 +7,8 @@ namespace psatd {
 constexpr int kMaxDft = 16;       // largest register DFT
 constexpr int kThreads = 256;     // threads per CTA of every stage kernel
 constexpr int kSegSmem = 64;      // exchange segments staged in shared memory per CTA
+constexpr int kPlaneSmemMax = 216 * 1024;   // dynamic shared memory of one stage tile (the rest: static)
+constexpr int kSplitRowBytes = 32 * 1024;   // row block of the split-plane schedule
 
 // Default split n = f1 * f2 of an FFT length (both factors in 1..16): the
 // most balanced pair, then the larger f1; 0 if none exists.
@@ -66,11 +68,13 @@ struct SubDesc {
     int64_t tab_ph;      // complex offset of stagger phases (same layout), or -1
     int seg_begin, seg_end;     // exchange segments whose source is this subdomain
     int64_t itemA, itemB, itemC; // first work item of this subdomain in each stage
+    int64_t itemA2, itemC1;      // split-plane schedule: first items of the column stages
     int ngz;             // guard cells per side along z (0 for 2D problems)
     int chunkB;          // modes per pass-B chunk (M)
     int lgB;             // log2(M) when M is a power of two, else -1
     int fsB;             // padded stride between fields of a pass-B chunk in shared memory
-    int pad1;
+    int rows;            // split-plane schedule: rows per x-transform item
+    int cols;            // split-plane schedule: columns per y-transform item
 };
 
 // A box of source valid cells copied into a destination local box.
@@ -94,7 +98,8 @@ struct LaunchCommon {
     unsigned long long* work;   // persistent-launch work counter (in the workspace)
     int persistent;             // 1: persistent grids drawing tickets; 0: one CTA per work item
     int nsub, nseg, nf, staggered, own_only;
-    int64_t per_sub[3];   // items per subdomain of passes A, B, C when every subdomain has the same shape, else 0
+    int64_t per_sub[5];   // items per subdomain of passes A, B, C and of the split schedule's column stages
+                          // (forward, inverse) when every subdomain has the same shape, else 0
     int variant;          // index into kFixedF32 / kFixedF64, or -1 for the descriptor-driven kernels
 };
 

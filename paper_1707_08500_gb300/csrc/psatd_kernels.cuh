@@ -82,7 +82,7 @@ struct Args {
     unsigned long long* work;   // work-item ticket counter of this launch (zeroed before it)
     int persistent;         // 1: CTAs draw items from `work`; 0: CTA b does item item0 + b
     int64_t item0, nitems;  // items handled by this launch
-    int64_t per_sub[3];     // items per subdomain of each stage when uniform, else 0
+    int64_t per_sub[5];     // items per subdomain of each stage when uniform, else 0
     int nsub, nseg;
     int nf;                 // fields transformed forward (9, or 10 with rho)
     int staggered;
@@ -260,9 +260,69 @@ __device__ __forceinline__ void split_pair(int i, int h, int f2, int& pa, int& p
     else { pa = f2 + (i - lower - 1); pb = h + f2 - 1 - pa; }
 }
 
+// Stages: 0 = pass A, 1 = pass B, 2 = pass C, 3 = standalone exchange; the
+// split-plane schedule replaces A by 4 (x rows) + 5 (y columns) and C by
+// 6 (y columns) + 7 (x rows and the exchange scatter).
 template <int STAGE>
 __device__ __forceinline__ int64_t stage_item(const SubDesc& d) {
-    return STAGE == 0 ? d.itemA : STAGE == 1 ? d.itemB : d.itemC;
+    return STAGE == 0 || STAGE == 4 ? d.itemA : STAGE == 1 ? d.itemB : STAGE == 5 ? d.itemA2
+         : STAGE == 6 ? d.itemC1 : d.itemC;
+}
+
+// Slot of LaunchCommon::per_sub that counts a stage's items per subdomain.
+template <int STAGE>
+constexpr int per_sub_slot() {
+    return STAGE == 0 || STAGE == 4 ? 0 : STAGE == 1 ? 1 : STAGE == 5 ? 3 : STAGE == 6 ? 4 : 2;
+}
+
+// Real split after the packed forward x transform: rows r < nrows at
+// p0 + r*pitch hold the h-point transform of z[m] = x[2m] + i x[2m+1] in
+// position order; each becomes the half spectrum X[0..h] of its real row,
+// walking the pairs (k, h-k) directly in position order (see split_pair).
+template <typename T>
+__device__ __forceinline__ void real_split_rows(cpx<T>* p0, int nrows, int pitch, int h, int f2x,
+                                                const twd<T>* __restrict__ wp) {
+    loop2(nrows, split_pairs(h, f2x), [&](int i, int y) {
+        cpx<T>* p = p0 + y * pitch;
+        if (i == 0) {
+            const cpx<T> z0 = p[0];
+            p[0] = mk(z0.x + z0.y, T(0));
+            p[h] = mk(z0.x - z0.y, T(0));
+        } else {
+            int pa, pb;
+            split_pair(i, h, f2x, pa, pb);
+            const cpx<T> A = p[pa], Bc = conj(p[pb]);
+            const cpx<T> e = scale(A + Bc, T(0.5));
+            const cpx<T> dd = A - Bc;
+            const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);   // (A - conj B)/(2i)
+            const cpx<T> wo = mul_tw(o, ld_tw(wp + pa));
+            p[pa] = e + wo;
+            if (pb != pa) p[pb] = conj(e - wo);
+        }
+    });
+}
+
+// Inverse of real_split_rows before the inverse x transform: merge each row's
+// half spectrum into the packed h-point form (C2R: only the real parts of
+// X[0] and X[h] are used).
+template <typename T>
+__device__ __forceinline__ void real_merge_rows(cpx<T>* p0, int nrows, int pitch, int h, int f2x,
+                                                const twd<T>* __restrict__ wp) {
+    loop2(nrows, split_pairs(h, f2x), [&](int i, int y) {
+        cpx<T>* p = p0 + y * pitch;
+        if (i == 0) {
+            const T x0 = p[0].x, xh = p[h].x;
+            p[0] = mk(x0 + xh, x0 - xh);
+        } else {
+            int pa, pb;
+            split_pair(i, h, f2x, pa, pb);
+            const cpx<T> A = p[pa], Bc = conj(p[pb]);
+            const cpx<T> e = A + Bc;
+            const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + pa));
+            p[pa] = e + mul_i(o);
+            if (pb != pa) p[pb] = conj(e) + mul_i(conj(o));
+        }
+    });
 }
 
 template <int STAGE>
@@ -284,8 +344,8 @@ __device__ __forceinline__ int decode_item(const Args<T>& a, int64_t it, SubDesc
     __shared__ int s_sub;
     if (threadIdx.x < 32) {
         int s = 0;
-        if (a.per_sub[STAGE] > 0) {
-            s = int(it / a.per_sub[STAGE]);
+        if (a.per_sub[per_sub_slot<STAGE>()] > 0) {
+            s = int(it / a.per_sub[per_sub_slot<STAGE>()]);
         } else if (threadIdx.x == 0) {
             s = find_sub<STAGE>(a.subs, a.nsub, it);
         }
@@ -377,28 +437,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
         fft_fwd<false>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1, 1}, a.tw);
-        // split the packed transform into the half spectrum X[0..h], walking
-        // the pairs (k, h-k) directly in position order (see split_pair)
-        const twd<T>* wp = a.tw + d.tw_post;
-        const int f2x = g.ax.f2;
-        loop2(Ly, split_pairs(h, f2x), [&](int i, int y) {
-            cpx<T>* p = sm + y * pitch;
-            if (i == 0) {
-                const cpx<T> z0 = p[0];
-                p[0] = mk(z0.x + z0.y, T(0));
-                p[h] = mk(z0.x - z0.y, T(0));
-            } else {
-                int pa, pb;
-                split_pair(i, h, f2x, pa, pb);
-                const cpx<T> A = p[pa], Bc = conj(p[pb]);
-                const cpx<T> e = scale(A + Bc, T(0.5));
-                const cpx<T> dd = A - Bc;
-                const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);   // (A - conj B)/(2i)
-                const cpx<T> wo = mul_tw(o, ld_tw(wp + pa));
-                p[pa] = e + wo;
-                if (pb != pa) p[pb] = conj(e - wo);
-            }
-        });
+        // split the packed transform into the half spectrum X[0..h]
+        real_split_rows(sm, Ly, pitch, h, g.ax.f2, a.tw + d.tw_post);
         __syncthreads();
         // y: complex FFT of length Ly over the lxh columns
         fft_fwd<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
@@ -578,24 +618,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
         __syncthreads();
         fft_inv<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
-        const twd<T>* wp = a.tw + d.tw_post;
-        const int f2x = g.ax.f2;
         cpx<T>* rows = sm + ng * pitch;
-        loop2(ny, split_pairs(h, f2x), [&](int i, int y) {
-            cpx<T>* p = rows + y * pitch;
-            if (i == 0) {
-                const T x0 = p[0].x, xh = p[h].x;        // real parts only (C2R)
-                p[0] = mk(x0 + xh, x0 - xh);
-            } else {
-                int pa, pb;
-                split_pair(i, h, f2x, pa, pb);
-                const cpx<T> A = p[pa], Bc = conj(p[pb]);
-                const cpx<T> e = A + Bc;
-                const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + pa));
-                p[pa] = e + mul_i(o);
-                if (pb != pa) p[pb] = conj(e) + mul_i(conj(o));
-            }
-        });
+        real_merge_rows(rows, ny, pitch, h, g.ax.f2, a.tw + d.tw_post);
         __syncthreads();
         fft_inv<false>(rows, g.ax, Batch{ny, pitch, 0, 0, 1, 1}, a.tw);
         // store the valid cells of this plane to every box that holds them
@@ -616,6 +640,146 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
                 });
             } else {
                 loop2(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
+            }
+        }
+        __syncthreads();
+    }
+}
+
+
+// ---- split-plane schedule: planes larger than shared memory -----------------
+// Passes A and C stage a whole (x, y) plane of one field in shared memory.
+// When a plane does not fit (a large box, e.g. one box over the whole grid,
+// the global solver), each of them is done in two launches instead: row
+// items transform a block of `rows` rows of a plane along x, column items
+// transform `cols` half-spectrum columns of a plane along y in place in the
+// spectra block.  Pass B is unchanged.  Forward: stage 4 (x rows, real split)
+// then stage 5 (y columns); inverse: stage 6 (y columns, valid rows stored)
+// then stage 7 (real merge, x rows, the exchange scatter of pass C).
+
+// stage 4: x (real) transforms of a block of rows of one input plane
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
+        decode_item<4>(a, it, &d);
+        const GeoDyn g(d);
+        const int R = d.rows, nb = (g.Ly + R - 1) / R;
+        const int loc = int(it - d.itemA);
+        const int pl = loc / nb, rb = loc - pl * nb;
+        const int f = pl / g.Lz, z = pl - f * g.Lz;
+        const int y0 = rb * R, nr = min(R, g.Ly - y0);
+        const int h = g.h, pitch = g.pitch, lxh = g.lxh;
+        const cpx<T>* src = reinterpret_cast<const cpx<T>*>(field_in(a, f) + d.field_off +
+                                                            (int64_t(z) * g.Ly + y0) * g.Lx);
+        loop2(h, nr, [&](int y, int m) { cp_async_c(sm + y * pitch + m, src + y * h + m); });
+        cp_async_wait_all();
+        __syncthreads();
+        fft_fwd<false>(sm, g.ax, Batch{nr, pitch, 0, 0, 1, 1}, a.tw);
+        real_split_rows(sm, nr, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        __syncthreads();
+        cpx<T>* dst = a.spec + d.spec_off + int64_t(f * g.Lz + z) * g.q + int64_t(y0) * lxh;
+        loop2(lxh, nr, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
+        __syncthreads();
+    }
+}
+
+// stages 5 (forward, every plane of the nf input fields) and 6 (inverse, the
+// valid z planes of the six outputs): y transforms of `cols` columns of one
+// plane; the inverse stores only the valid rows, the only ones stage 7 reads
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads) k_cols(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
+        decode_item<INV ? 6 : 5>(a, it, &d);
+        const GeoDyn g(d);
+        const int W = d.cols, lxh = g.lxh, Ly = g.Ly, nb = (lxh + W - 1) / W;
+        const int loc = int(it - (INV ? d.itemC1 : d.itemA2));
+        const int pl = loc / nb, cb = loc - pl * nb;
+        int f, z;
+        if (INV) { f = pl / g.nvz; z = g.ngz + (pl - f * g.nvz); }
+        else { f = pl / g.Lz; z = pl - f * g.Lz; }
+        const int c0 = cb * W, wc = min(W, lxh - c0);
+        cpx<T>* base = a.spec + d.spec_off + int64_t(f * g.Lz + z) * g.q + c0;
+        loop2(W, Ly, [&](int y, int m) {
+            const cpx<T>* src = base + int64_t(y) * lxh + (m < wc ? m : 0);
+            if constexpr (sizeof(T) == 4) cp_async8z(sm + y * W + m, src, m < wc ? 8 : 0);
+            else cp_async16(sm + y * W + m, src, m < wc ? 16 : 0);
+        });
+        cp_async_wait_all();
+        __syncthreads();
+        if constexpr (INV) fft_inv<false>(sm, g.ay, Batch{W, 1, 0, 0, W, 1}, a.tw);
+        else fft_fwd<false>(sm, g.ay, Batch{W, 1, 0, 0, W, 1}, a.tw);
+        const int ya = INV ? g.ng : 0, ny = INV ? g.nvy : Ly;
+        loop2(W, ny, [&](int y, int m) {
+            if (m < wc) stcs_c(base + int64_t(ya + y) * lxh + m, sm[(ya + y) * W + m]);
+        });
+        __syncthreads();
+    }
+}
+
+// stage 7: real merge and inverse x transforms of a block of valid rows of one
+// output plane, then the store of pass C (own box and every guard image)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rows_inv(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
+    __shared__ Segment segs[kSegSmem];
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
+        decode_item<7>(a, it, &d);
+        const GeoDyn g(d);
+        const int R = d.rows, nb = (g.nvy + R - 1) / R;
+        const int loc = int(it - d.itemC);
+        const int pl = loc / nb, rb = loc - pl * nb;
+        const int f = pl / g.nvz, z = g.ngz + (pl - f * g.nvz);
+        const int ya = g.ng + rb * R, nr = min(R, g.ng + g.nvy - ya);
+        const int h = g.h, pitch = g.pitch, lxh = g.lxh;
+        const cpx<T>* src = a.spec + d.spec_off + int64_t(f * g.Lz + z) * g.q + int64_t(ya) * lxh;
+        loop2(lxh, nr, [&](int y, int c) { cp_async_c(sm + y * pitch + c, src + y * lxh + c); });
+        const int nsg = min(d.seg_end - d.seg_begin, kSegSmem);
+        {
+            const int* gs = reinterpret_cast<const int*>(a.segs + d.seg_begin);
+            int* ss = reinterpret_cast<int*>(segs);
+            for (int i = threadIdx.x; i < nsg * int(sizeof(Segment) / 4); i += kThreads) ss[i] = __ldg(gs + i);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        real_merge_rows(sm, nr, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        __syncthreads();
+        fft_inv<false>(sm, g.ax, Batch{nr, pitch, 0, 0, 1, 1}, a.tw);
+        T* out = a.eb[f];
+        const T* rp = reinterpret_cast<const T*>(sm);
+        const int rs = 2 * pitch;                         // real row stride
+        for (int k = 0; k < d.seg_end - d.seg_begin; ++k) {
+            const Segment& sg = k < kSegSmem ? segs[k] : a.segs[d.seg_begin + k];
+            if (a.own_only && !sg.identity) continue;
+            if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
+            const int y_lo = max(sg.y0, ya), y_hi = min(sg.y0 + sg.ey, ya + nr);
+            if (y_lo >= y_hi) continue;
+            T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + y_lo + sg.dy) * sg.dLx + sg.x0 + sg.dx;
+            const T* sp = rp + (y_lo - ya) * rs + sg.x0;
+            if (sg.vec4) {
+                loop2(sg.ex >> 2, y_hi - y_lo, [&](int yy, int x4) {
+                    const cpx<T> u = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4);
+                    const cpx<T> w = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4 + 2);
+                    stcs4(dst + int64_t(yy) * sg.dLx + 4 * x4, cpx4<T>{u.x, u.y, w.x, w.y});
+                });
+            } else {
+                loop2(sg.ex, y_hi - y_lo, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
             }
         }
         __syncthreads();
@@ -682,7 +846,7 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     a.work = c.work;
     a.persistent = c.persistent;
     a.item0 = item0;
-    for (int i = 0; i < 3; ++i) a.per_sub[i] = c.per_sub[i];
+    for (int i = 0; i < 5; ++i) a.per_sub[i] = c.per_sub[i];
     a.nitems = nitems;
     a.nsub = c.nsub;
     a.nseg = c.nseg;
@@ -700,17 +864,15 @@ static inline cudaError_t set_smem_attr(const void* fn, int bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-// Launch pass A, B or C with geometry G (stage 0, 1, 2) or the exchange (3).
-template <typename T, class G>
-static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_t st) {
-    const void* fn = stage == 0 ? (const void*)k_pass_a<T, G> : stage == 1 ? (const void*)k_pass_b<T, G>
-                   : stage == 2 ? (const void*)k_pass_c<T, G> : (const void*)k_exchange<T>;
+// One launch of kernel k: persistent (as many CTAs as can be resident, each
+// drawing work items from the ticket counter) or one CTA per item.
+template <typename T>
+static cudaError_t launch_kernel(void (*k)(Args<T>), const Args<T>& a, int smem, cudaStream_t st) {
+    const void* fn = (const void*)k;
     cudaError_t e = set_smem_attr(fn, smem);
     if (e != cudaSuccess) return e;
     unsigned grid = grid_for(a.nitems);
     if (a.persistent) {
-        // one persistent launch: as many CTAs as can be resident, each drawing
-        // work items from the ticket counter
         int per_sm = 0, dev = 0, nsm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -719,13 +881,24 @@ static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_
         grid = grid_for(a.nitems < resident ? a.nitems : resident);
         if ((e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     }
-    switch (stage) {
-        case 0: k_pass_a<T, G><<<grid, kThreads, smem, st>>>(a); break;
-        case 1: k_pass_b<T, G><<<grid, kThreads, smem, st>>>(a); break;
-        case 2: k_pass_c<T, G><<<grid, kThreads, smem, st>>>(a); break;
-        default: k_exchange<T><<<grid, kThreads, 0, st>>>(a); break;
-    }
+    k<<<grid, kThreads, smem, st>>>(a);
     return cudaPeekAtLastError();
+}
+
+// Launch stage `stage` (see stage_item) with geometry G; the exchange and the
+// split-plane stages always read the geometry from the descriptors.
+template <typename T, class G>
+static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_t st) {
+    switch (stage) {
+        case 0: return launch_kernel<T>(k_pass_a<T, G>, a, smem, st);
+        case 1: return launch_kernel<T>(k_pass_b<T, G>, a, smem, st);
+        case 2: return launch_kernel<T>(k_pass_c<T, G>, a, smem, st);
+        case 4: return launch_kernel<T>(k_rows_fwd<T>, a, smem, st);
+        case 5: return launch_kernel<T>(k_cols<T, false>, a, smem, st);
+        case 6: return launch_kernel<T>(k_cols<T, true>, a, smem, st);
+        case 7: return launch_kernel<T>(k_rows_inv<T>, a, smem, st);
+        default: return launch_kernel<T>(k_exchange<T>, a, 0, st);
+    }
 }
 
 }  // namespace psatd

@@ -9,7 +9,7 @@ using GeoF32 = GeoFix<kFixedF32[I].L, kFixedF32[I].ng, kFixedF32[I].M, 8>;
 cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t item0, int64_t nitems, int smem, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const Args<float> a = make_args<float>(c, item0, nitems);
-    if (stage == 3) return launch_geo<float, GeoDyn>(stage, a, 0, st);
+    if (stage >= 3) return launch_geo<float, GeoDyn>(stage, a, smem, st);
     switch (c.variant) {
         case 0: return launch_geo<float, GeoF32<0>>(stage, a, smem, st);
         case 1: return launch_geo<float, GeoF32<1>>(stage, a, smem, st);

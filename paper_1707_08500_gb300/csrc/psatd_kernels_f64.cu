@@ -9,7 +9,7 @@ using GeoF64 = GeoFix<kFixedF64[I].L, kFixedF64[I].ng, kFixedF64[I].M, 16>;
 cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t item0, int64_t nitems, int smem, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const Args<double> a = make_args<double>(c, item0, nitems);
-    if (stage == 3) return launch_geo<double, GeoDyn>(stage, a, 0, st);
+    if (stage >= 3) return launch_geo<double, GeoDyn>(stage, a, smem, st);
     switch (c.variant) {
         case 0: return launch_geo<double, GeoF64<0>>(stage, a, smem, st);
         case 1: return launch_geo<double, GeoF64<1>>(stage, a, smem, st);

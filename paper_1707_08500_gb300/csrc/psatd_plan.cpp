@@ -126,11 +126,12 @@ struct psatd_plan_s {
     std::vector<TabKey> tab_keys;
     std::vector<int64_t> tab_coef_off, tab_k_off, tab_ph_off;
     int64_t n_tab = 0, n_tabc = 0;
-    int64_t items[3] = {0, 0, 0};
+    int64_t items[5] = {0, 0, 0, 0, 0};   // stages A (or x rows), B, C (or x rows), y columns fwd, inv
     int64_t exch_items = 0;
-    int64_t per_sub[3] = {0, 0, 0};   // items per subdomain when uniform
+    int64_t per_sub[5] = {0, 0, 0, 0, 0};   // items per subdomain when uniform
     int variant = -1;                  // compile-time geometry variant, or -1
-    int smemA = 0, smemB = 0, smemC = 0;
+    int smemA = 0, smemB = 0, smemC = 0, smemR = 0, smemK = 0;
+    bool split = false;                // split-plane schedule (row and column launches)
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_work = 0, off_spec = 0, ws_need = 0;
     int64_t spec_elems = 0;
@@ -300,7 +301,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     auto bad = [&](int code, const std::string& m) { int c = fail(p, code, m); delete p; return c; };
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
-    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D))
+    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D | PSATD_SPLIT_PLANES))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -430,7 +431,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     }
     // --- pass-B chunk, shared memory, work items --------------------------------
     const int csz = p->f64 ? 16 : 8;
-    int64_t iA = 0, iB = 0, iC = 0, spec = 0, maxspec = 0;
+    int64_t iA = 0, iB = 0, iC = 0, iA2 = 0, iC1 = 0, spec = 0, maxspec = 0;
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
         int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
@@ -449,25 +450,46 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         p->smemA = std::max(p->smemA, d.L[1] * d.pitch * csz);
         p->smemC = p->smemA;
         p->smemB = std::max(p->smemB, p->nf * d.fsB * csz);
-        d.itemA = iA; iA += int64_t(p->nf) * d.L[2];
-        d.itemB = iB; iB += (d.q + M - 1) / M;
-        d.itemC = iC; iC += 6 * int64_t(d.nv[2]);
         int64_t sp = int64_t(p->nf) * d.L[2] * d.q;
         d.spec_off = p->plain ? 0 : spec;
         spec += int64_t(align_up(sp, 32));
         maxspec = std::max<int64_t>(maxspec, int64_t(align_up(sp, 32)));
     }
-    p->items[0] = iA; p->items[1] = iB; p->items[2] = iC;
+    // planes that do not fit in shared memory take the split-plane schedule:
+    // x rows and y columns in separate launches (stages 4-7 of the kernels)
+    p->split = (flags & PSATD_SPLIT_PLANES) || p->smemA > kPlaneSmemMax;
+    for (int s = 0; s < nsub; ++s) {
+        SubDesc& d = p->desc[s];
+        d.itemA = iA; d.itemB = iB; d.itemC = iC;
+        d.rows = d.L[1];
+        d.cols = d.lxh;
+        if (p->split) {
+            d.rows = std::max(1, std::min(d.L[1], kSplitRowBytes / (d.pitch * csz)));
+            d.cols = std::min(d.lxh, p->f64 ? 8 : 16);
+            d.itemA2 = iA2; d.itemC1 = iC1;
+            const int64_t rb_in = (d.L[1] + d.rows - 1) / d.rows, rb_out = (d.nv[1] + d.rows - 1) / d.rows;
+            const int64_t cb = (d.lxh + d.cols - 1) / d.cols;
+            iA += int64_t(p->nf) * d.L[2] * rb_in;
+            iA2 += int64_t(p->nf) * d.L[2] * cb;
+            iC1 += 6 * int64_t(d.nv[2]) * cb;
+            iC += 6 * int64_t(d.nv[2]) * rb_out;
+            p->smemR = std::max(p->smemR, d.rows * d.pitch * csz);
+            p->smemK = std::max(p->smemK, d.L[1] * d.cols * csz);
+        } else {
+            iA += int64_t(p->nf) * d.L[2];
+            iC += 6 * int64_t(d.nv[2]);
+        }
+        iB += (d.q + d.chunkB - 1) / d.chunkB;
+    }
+    p->items[0] = iA; p->items[1] = iB; p->items[2] = iC; p->items[3] = iA2; p->items[4] = iC1;
     {
         bool uni = true;
         const SubDesc& d0 = p->desc[0];
         for (const SubDesc& d : p->desc)
-            uni = uni && d.L[0] == d0.L[0] && d.L[1] == d0.L[1] && d.L[2] == d0.L[2] && d.nv[2] == d0.nv[2] && d.chunkB == d0.chunkB;
-        if (uni) {
-            p->per_sub[0] = int64_t(p->nf) * d0.L[2];
-            p->per_sub[1] = (d0.q + d0.chunkB - 1) / d0.chunkB;
-            p->per_sub[2] = 6 * int64_t(d0.nv[2]);
-        }
+            uni = uni && d.L[0] == d0.L[0] && d.L[1] == d0.L[1] && d.L[2] == d0.L[2] && d.nv[1] == d0.nv[1] &&
+                  d.nv[2] == d0.nv[2] && d.chunkB == d0.chunkB && d.rows == d0.rows && d.cols == d0.cols;
+        if (uni)
+            for (int k = 0; k < 5; ++k) p->per_sub[k] = p->items[k] / nsub;
     }
     p->spec_elems = p->plain ? maxspec : spec;
     // kernels with compile-time geometry apply when every subdomain is the
@@ -475,7 +497,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     {
         const FixedGeo* list = p->f64 ? kFixedF64 : kFixedF32;
         const int nl = p->f64 ? int(sizeof(kFixedF64) / sizeof(FixedGeo)) : int(sizeof(kFixedF32) / sizeof(FixedGeo));
-        for (int v = 0; v < nl && p->variant < 0; ++v) {
+        for (int v = 0; v < nl && p->variant < 0 && !p->split; ++v) {
             const int L = list[v].L, g = list[v].ng, M = list[v].M;
             bool ok = true;
             for (const SubDesc& d : p->desc) {
@@ -487,8 +509,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
             if (ok) p->variant = v;
         }
     }
-    if (std::max(p->smemA, p->smemB) > 227 * 1024)
-        return bad(PSATD_E_UNSUPPORTED, "a local plane does not fit in shared memory");
+    if (p->smemB > kPlaneSmemMax || (p->split && std::max(p->smemR, p->smemK) > kPlaneSmemMax))
+        return bad(PSATD_E_UNSUPPORTED, "a stage's tile does not fit in shared memory");
     // --- exchange segments (source valid box -> destination local box) ----------
     for (int s = 0; s < nsub; ++s) {
         p->desc[s].seg_begin = int(p->segs.size());
@@ -588,7 +610,8 @@ int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
 int psatd_push_launches(psatd_plan_t p, int32_t* n) {
     if (!p || !n) return PSATD_E_ARG;
     int nsub = int(p->desc.size());
-    *n = p->plain ? 3 * nsub + (p->exch_items > 0 ? 1 : 0) : 3;
+    const int per = p->split ? 5 : 3;
+    *n = p->plain ? per * nsub + (p->exch_items > 0 ? 1 : 0) : per;
     if (p->diag) *n += 1;
     return PSATD_OK;
 }
@@ -663,7 +686,7 @@ static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f
     c.nf = p->nf;
     c.staggered = p->stag ? 1 : 0;
     c.own_only = 0;
-    for (int i = 0; i < 3; ++i) c.per_sub[i] = p->per_sub[i];
+    for (int i = 0; i < 5; ++i) c.per_sub[i] = p->per_sub[i];
     c.variant = p->variant;
     return c;
 }
@@ -704,20 +727,45 @@ static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaS
     };
     cudaError_t e = cudaSuccess;
     if ((e = mark(0)) != cudaSuccess) return cuda_fail(p, e, "event record");
+    // the forward stages, pass B and the inverse stages over items [i0, i0+n)
+    // of each (n < 0: every item of the stage)
+    struct Range { int64_t a0, an, a20, a2n, b0, bn, c10, c1n, c0, cn; };
+    auto run = [&](const Range& r) -> int {
+        if (!p->split) {
+            if ((e = stage(p, 0, c, r.a0, r.an, p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
+        } else {
+            if ((e = stage(p, 4, c, r.a0, r.an, p->smemR, s)) != cudaSuccess) return cuda_fail(p, e, "x rows launch");
+            if ((e = stage(p, 5, c, r.a20, r.a2n, p->smemK, s)) != cudaSuccess) return cuda_fail(p, e, "y columns launch");
+        }
+        if (!p->plain && (e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
+        if ((e = stage(p, 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        if (!p->plain && (e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
+        if (!p->split) {
+            if ((e = stage(p, 2, c, r.c0, r.cn, p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+        } else {
+            if ((e = stage(p, 6, c, r.c10, r.c1n, p->smemK, s)) != cudaSuccess) return cuda_fail(p, e, "y columns launch");
+            if ((e = stage(p, 7, c, r.c0, r.cn, p->smemR, s)) != cudaSuccess) return cuda_fail(p, e, "x rows launch");
+        }
+        return PSATD_OK;
+    };
     if (!p->plain) {
-        if ((e = stage(p, 0, c, 0, p->items[0], p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
-        if ((e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
-        if ((e = stage(p, 1, c, 0, p->items[1], p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
-        if ((e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
-        if ((e = stage(p, 2, c, 0, p->items[2], p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+        int r = run(Range{0, p->items[0], 0, p->items[3], 0, p->items[1], 0, p->items[4], 0, p->items[2]});
+        if (r) return r;
     } else {
         c.own_only = 1;
         const int nsub = int(p->desc.size());
         for (int i = 0; i < nsub; ++i) {
             const SubDesc& d = p->desc[i];
-            if ((e = stage(p, 0, c, d.itemA, int64_t(p->nf) * d.L[2], p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
-            if ((e = stage(p, 1, c, d.itemB, (d.q + d.chunkB - 1) / d.chunkB, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
-            if ((e = stage(p, 2, c, d.itemC, 6 * int64_t(d.nv[2]), p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+            // item ranges of subdomain i: up to the next subdomain's first items
+            const bool last = i + 1 == nsub;
+            const SubDesc* n = last ? nullptr : &p->desc[i + 1];
+            Range g{d.itemA, (last ? p->items[0] : n->itemA) - d.itemA,
+                    d.itemA2, (last ? p->items[3] : n->itemA2) - d.itemA2,
+                    d.itemB, (last ? p->items[1] : n->itemB) - d.itemB,
+                    d.itemC1, (last ? p->items[4] : n->itemC1) - d.itemC1,
+                    d.itemC, (last ? p->items[2] : n->itemC) - d.itemC};
+            int r = run(g);
+            if (r) return r;
         }
         if ((e = stage(p, 3, c, 0, p->exch_items, 0, s)) != cudaSuccess) return cuda_fail(p, e, "exchange launch");
     }

@@ -167,6 +167,8 @@ def workload(name: str) -> Workload:
     broadband256 : 256^3, 4x4x4 x 64^3, ng=16, p=64, FP32, 100 steps
     uneven48     : 192x144x192, 48 uneven subdomains, ng in {8,16}, p in {16,32,64}, FP32, 50 steps
     mirror1024   : 1024x512x512, 16x8x8 x 64^3, ng=16, p=100, FP32, 100 steps (plasma-mirror shaped)
+    global256    : broadband256 as one 256^3 box without guards (the global solver), FP32
+    broadband2d  : 4096^2 (2D), 64x64 x 64^2, ng=16, p=64, FP32
     """
     if name == "plain32":
         return Workload(name, (32, 32, 32), tensor_decomposition([32], [32], [32], 0, 0),
@@ -194,10 +196,21 @@ def workload(name: str) -> Workload:
         return Workload(name, (1024, 512, 512),
                         tensor_decomposition([64] * 16, [64] * 8, [64] * 8, 16, 100),
                         "laser_slab", 100, "f32", 1707 + 5)
+    if name == "global256":
+        # broadband256's grid and fields as one box without guards: the global
+        # solver (Fig. 2b) on one GPU
+        return Workload(name, (256, 256, 256), [Sub((0, 0, 0), (256, 256, 256), 0, 64)],
+                        "broadband", 100, "f32", 1707 + 3)
+    if name == "broadband2d":
+        # a 2D problem: 4096^2 cells in 64 x 64 subdomains of 64^2, 16 guards
+        subs = [dataclasses.replace(sd, zguard=False)
+                for sd in tensor_decomposition([64] * 64, [64] * 64, [1], 16, 64)]
+        return Workload(name, (4096, 4096, 1), subs, "broadband", 100, "f32", 1707 + 6, two_d=True)
     raise KeyError(name)
 
 
 WORKLOADS = ("plain32", "yee64", "broadband256", "uneven48", "mirror1024")
+EXTRA_WORKLOADS = ("global256", "broadband2d")     # the global solver and a 2D problem
 
 
 def custom(name, global_n, cuts, ng, p, fields="broadband", steps=1, precision="f32",

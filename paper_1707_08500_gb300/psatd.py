@@ -25,6 +25,7 @@ PSATD_GAUSS_DIAG = 0x08
 PSATD_PLAIN = 0x10
 PSATD_GRID_PER_ITEM = 0x20
 PSATD_2D = 0x40
+PSATD_SPLIT_PLANES = 0x80
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}
@@ -272,9 +273,10 @@ class Solver:
         box from global arrays [Nz][Ny][Nx] (periodic indexing)."""
         names = names or _inputs.FIELD_NAMES
         nx, ny, nz = self.wl.global_n
+        dev = {n: glob[n].to(self.device) for n in names}
         for s, sd in enumerate(self.wl.subs):
             for n in names:
-                g = glob[n].to(self.device)
+                g = dev[n]
                 b = self.box(n, s)
                 gx, gy, gz = sd.guards
                 if guards:

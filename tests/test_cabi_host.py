@@ -170,3 +170,33 @@ def test_two_d_plans(P):
     with pytest.raises(P.PsatdError) as e:
         P.psatd_plan_create((32, 32, 32), subs, P.PSATD_F32 | P.PSATD_2D)
     assert e.value.code == -2
+
+
+def test_split_plane_schedule_is_chosen_for_large_planes(P):
+    """One box over a 256^3 grid (PSATD-global, Fig. 2b): its (x, y) plane
+    does not fit in shared memory, so the plan takes the five-stage
+    split-plane schedule; a 64^3 box takes it only when forced."""
+    g = (256, 256, 256)
+    subs = [I.Sub((0, 0, 0), g, 0, 64)]
+    for flags, want in ((P.PSATD_F32, 5), (P.PSATD_F64, 5), (P.PSATD_F32 | P.PSATD_GAUSS_DIAG, 6),
+                        (P.PSATD_F32 | P.PSATD_PLAIN, 5)):
+        h = P.psatd_plan_create(g, subs, flags)
+        try:
+            assert P.psatd_push_launches(h) == want
+            assert P.psatd_geometry_variant(h) == -1
+            assert P.psatd_layout(h, 0)[1] == g
+        finally:
+            P.psatd_destroy(h)
+    wl = I.workload("broadband256")
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32)
+    assert P.psatd_push_launches(h) == 3
+    P.psatd_destroy(h)
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32 | P.PSATD_SPLIT_PLANES)
+    assert P.psatd_push_launches(h) == 5 and P.psatd_geometry_variant(h) == -1
+    P.psatd_destroy(h)
+    # the largest boxes: x half length and y, z lengths up to 16 x 16
+    h = P.psatd_plan_create((512, 256, 256), [I.Sub((0, 0, 0), (512, 256, 256), 0, 0)], P.PSATD_F32)
+    P.psatd_destroy(h)
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_plan_create((1024, 256, 256), [I.Sub((0, 0, 0), (1024, 256, 256), 0, 0)], P.PSATD_F32)
+    assert e.value.code == -5

@@ -29,8 +29,9 @@ def _np(d):
     return {k: v.numpy() if isinstance(v, torch.Tensor) else v for k, v in d.items()}
 
 
-def _run_gpu(P, wl, glob, steps, plain=False, gauss=False, precision=None):
-    sol = P.Solver(wl, precision=precision, plain=plain, gauss=gauss)
+def _run_gpu(P, wl, glob, steps, plain=False, gauss=False, precision=None, split=False):
+    sol = P.Solver(wl, precision=precision, plain=plain, gauss=gauss,
+                   extra_flags=P.PSATD_SPLIT_PLANES if split else 0)
     sol.load_global(glob, names=I.EB_NAMES, guards=False)
     sol.load_global(glob, names=("Jx", "Jy", "Jz", "rho"), guards=True)
     sol.exchange()
@@ -89,12 +90,12 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("plain", [False, True])
-def test_push_matches_oracle(P, name, plain):
+@pytest.mark.parametrize("schedule", ["batched", "plain", "split", "split_plain"])
+def test_push_matches_oracle(P, name, schedule):
     make, steps, tol = CASES[name]
     wl = make()
     glob = I.global_fields(wl)
-    sol, _ = _run_gpu(P, wl, glob, steps, plain=plain)
+    sol, _ = _run_gpu(P, wl, glob, steps, plain="plain" in schedule, split="split" in schedule)
     ref, _ = _oracle(wl, glob, steps)
     got = _np(sol.gather_global())
     err = O.rel_l2(got, ref)
@@ -126,12 +127,13 @@ def _twod(precision):
                     precision=precision, two_d=True)
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("shape", ["3d", "2d"])
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 1e-3)])
-def test_gauss_partials_match_oracle(P, precision, tol, shape):
+def test_gauss_partials_match_oracle(P, precision, tol, shape, split):
     wl = _mixed(precision) if shape == "3d" else _twod(precision)
     glob = I.global_fields(wl)
-    _, gsum = _run_gpu(P, wl, glob, 2, gauss=True)
+    _, gsum = _run_gpu(P, wl, glob, 2, gauss=True, split=split)
     _, osum = _oracle(wl, glob, 2)
     for a, b in zip(gsum, osum):
         np.testing.assert_allclose(a[:, 1], b[:, 1], rtol=tol)        # |rho~|^2

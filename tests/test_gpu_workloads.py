@@ -91,7 +91,7 @@ def test_uneven48_one_step_f32_all_subdomains(P):
     np.testing.assert_allclose(sol.gauss_sums()[:, 1], np.array(gs)[:, 1], rtol=1e-3, atol=1e-6)
 
 
-def _sampled_check(P, wl, samples, tol):
+def _sampled_check(P, wl, samples, tol, variant=0):
     """One batched FP32 step on the full workload; every cell of the sampled
     subdomains' padded boxes (valid cells and the guard images written by the
     fused exchange) against the oracle's push of the subdomain that owns it.
@@ -116,13 +116,13 @@ def _sampled_check(P, wl, samples, tol):
     def box_of(td):
         if glob is None:
             return {k: v.numpy() for k, v in I.box_fields(wl, td, device="cpu").items()}
-        return {k: O.extract_box(v, td.lo, td.local, td.ng) for k, v in glob.items()}
+        return {k: O.extract_box(v, td.lo, td.local, O.sub_guards(td)) for k, v in glob.items()}
     sol.push()
     torch.cuda.synchronize()
-    assert P.psatd_geometry_variant(sol.plan) == 0
+    assert P.psatd_geometry_variant(sol.plan) == variant
     for s in samples:
         sd = wl.subs[s]
-        lo = [sd.lo[a] - sd.ng for a in range(3)]
+        lo = [sd.lo[a] - O.sub_guards(sd)[a] for a in range(3)]
         gidx = [(np.arange(sd.local[a]) + lo[a]) % wl.global_n[a] for a in range(3)]
         got = {n: sol.box(n, s).double().cpu().numpy() for n in I.EB_NAMES}
         covered = np.zeros(sd.local[::-1], dtype=bool)
@@ -133,8 +133,9 @@ def _sampled_check(P, wl, samples, tol):
                 continue
             out, _ = O.local_push(box_of(td), td.local, wl.dx, td.p, wl.c_dt, wl.staggered)
             sel = np.ix_(inx[2], inx[1], inx[0])
-            src = np.ix_(gidx[2][inx[2]] - td.lo[2] + td.ng, gidx[1][inx[1]] - td.lo[1] + td.ng,
-                         gidx[0][inx[0]] - td.lo[0] + td.ng)
+            tg = O.sub_guards(td)
+            src = np.ix_(gidx[2][inx[2]] - td.lo[2] + tg[2], gidx[1][inx[1]] - td.lo[1] + tg[1],
+                         gidx[0][inx[0]] - td.lo[0] + tg[0])
             num = sum(float(((got[n][sel] - out[n][src]) ** 2).sum()) for n in I.EB_NAMES)
             den = sum(float((out[n] ** 2).sum()) for n in I.EB_NAMES)
             worst = max(worst, (num / max(den, 1e-300)) ** 0.5)
@@ -156,6 +157,48 @@ def test_mirror1024_one_step_sampled(P):
     laser = next(s for s, sd in enumerate(wl.subs) if sd.lo == (256, 192, 192))
     slab = next(s for s, sd in enumerate(wl.subs) if sd.lo == (640, 256, 256))
     _sampled_check(P, wl, samples=[0, laser, slab], tol=2e-6)
+
+
+def test_broadband2d_one_step_sampled(P):
+    """The 2D workload (4096^2, 64 x 64 subdomains): a corner, an interior
+    and an edge subdomain."""
+    wl = I.workload("broadband2d")
+    _sampled_check(P, wl, samples=[0, 64 * 20 + 33, 64 * 63 + 5], tol=2e-6, variant=-1)
+
+
+def test_global256_f32_and_local_vs_global(P):
+    """Single-GPU PSATD-global (Fig. 2b): broadband256's grid and fields as one
+    256^3 box (split-plane schedule), 3 FP32 steps against the oracle's global
+    push.  Then the GPU-side local-vs-global difference after one step (the
+    4x4x4 decomposition with 16 guards against the global box) against the
+    same difference computed by the oracle."""
+    wg, wl = I.workload("global256"), I.workload("broadband256")
+    glob = I.global_fields(wl)
+    g = _np(glob)
+    sg = _solver(P, wg, glob)
+    assert P.psatd_push_launches(sg.plan) == 5
+    sg.push()
+    torch.cuda.synchronize()
+    one_g = _np(sg.gather_global())
+    for _ in range(2):
+        sg.push()
+    torch.cuda.synchronize()
+    got = _np(sg.gather_global())
+    ref, ref1 = g, None
+    for s in range(3):
+        ref = dict(ref, **O.global_push(ref, 64, wl.dx, wl.c_dt, False))
+        ref1 = ref if s == 0 else ref1
+    err = O.rel_l2(got, ref)
+    del sg
+    sl = _solver(P, wl, glob)
+    sl.push()
+    torch.cuda.synchronize()
+    d_gpu = O.rel_l2(_np(sl.gather_global()), one_g)
+    d_orc = O.rel_l2(O.step(g, wl), ref1)
+    print(f"global256 FP32 after 3 steps vs oracle: {err:.3e}; local vs global after 1 step: "
+          f"GPU {d_gpu:.4e}, oracle {d_orc:.4e}")
+    assert err < 1e-5
+    assert abs(d_gpu - d_orc) < 0.02 * d_orc
 
 
 @pytest.mark.parametrize("case", ["thin", "long_axis", "smallest"])
