@@ -201,6 +201,8 @@ def run_ours(args, rank, world, local_rank):
     flags = (P.PSATD_F32 if prec == "f32" else P.PSATD_F64) | (P.PSATD_GAUSS_DIAG if gauss else 0)
     if wl.staggered:
         flags |= P.PSATD_STAGGERED
+    if wl.two_d:
+        flags |= P.PSATD_2D
     if args.chunk_b:
         tuning = {"chunk_b": args.chunk_b, "f1": [0, 0, 0]}
     elif not args.no_tune:
@@ -272,7 +274,9 @@ def run_ours(args, rank, world, local_rank):
     by, local = stage_bytes(wl, nf, 4 if prec == "f32" else 8)
     peak, peak_kind = _peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    names = {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"}
+    split = P.psatd_push_launches(sol.plan) - (1 if gauss else 0) == 5
+    names = ({"A": "k_rows_fwd+k_cols", "B": "k_pass_b", "C": "k_cols+k_rows_inv"} if split
+             else {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"})
     stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
                    "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
     achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
@@ -286,7 +290,8 @@ def run_ours(args, rank, world, local_rank):
                    "local_n": list(wl.subs[0].local), "guards": wl.subs[0].ng, "order": wl.subs[0].p,
                    "c_dt": wl.c_dt, "gauss_diag": gauss, "valid_cells": valid, "local_cells": local,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "l2": "inputs (36 GB) larger than L2; no flush"},
+                   "schedule": "split-plane (5 stages)" if split else "3 stages",
+                   "l2": f"inputs ({local * nf * (4 if prec == 'f32' else 8) / 1e9:.1f} GB) larger than L2; no flush"},
         "local_gcell_steps": round(local * world / (ms_step / 1e3) / 1e9, 4),
         "stages": stages,
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
@@ -388,12 +393,127 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+YEE_METRIC = "Gcell-steps/s of the Yee FDTD step (Eqs. 2a/2b), FP32; % HBM roof"
+
+
+def run_yee(args, rank, world, local_rank):
+    """The Yee FDTD step (the paper's comparison solver) on the workload's
+    global grid: one fused kernel per step, fields ping-ponged between two
+    device sets.  Algorithmic bytes per cell: read E, B, J, write E, B."""
+    import torch
+    from paper_1707_08500_gb300 import build as B
+    from paper_1707_08500_gb300 import fdtd as F
+    from paper_1707_08500_gb300 import inputs as I
+    from paper_1707_08500_gb300 import psatd as P
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = I.workload(args.workload)
+    prec = args.precision or "f32"
+    esz = 4 if prec == "f32" else 8
+    dt = 0.5
+    sol = F.YeeSolver(wl.global_n, dt, wl.dx, precision=prec, device=dev)
+    glob = I.random_fields(wl.global_n, 1707 + 60, names=F.E_NAMES + F.B_NAMES + F.J_NAMES, device=dev)
+    sol.load(glob)
+    del glob
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+
+    def mkev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+    for _ in range(args.warmup):
+        sol.step(stream.cuda_stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0, t1 = mkev(), mkev()
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            sol.step(stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev) / args.steps
+    nx, ny, nz = wl.global_n
+    cells = nx * ny * nz
+    alg = 15 * esz * cells
+    peak, peak_kind = _peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    result = {
+        "metric": YEE_METRIC, "value": round(cells * world / (ms / 1e3) / 1e9, 3), "unit": "Gcell-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"yee-{wl.name}-grid", "global_n": list(wl.global_n), "c_dt": dt,
+                   "l2": f"fields ({15 * esz * cells / 1e9:.1f} GB per step) larger than L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "roofline": {"bound": "hbm", "kernel": "k_yee", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "alg_bytes_per_cell": 15 * esz},
+        "gpu_launches": args.steps * P.psatd_yee_launches(),
+        "clocks": clk.summary(),
+    }
+    if not args.skip_e2e:
+        host = {n: torch.empty_like(sol.J[n], device="cpu").pin_memory() for n in F.J_NAMES}
+        for n in F.J_NAMES:
+            host[n].copy_(sol.J[n])
+        probe = torch.empty((ny, nx), dtype=sol.dtype, pin_memory=True)
+        k = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0, e1 = mkev(), mkev()
+        e0.record(stream)
+        for _ in range(k):
+            for n in F.J_NAMES:
+                sol.J[n].copy_(host[n], non_blocking=True)
+            sol.step(stream.cuda_stream)
+            probe.copy_(sol.sets[sol.cur]["Ez"][nz // 2], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev) / k
+        result["e2e"] = {"value": round(cells * world / (ems / 1e3) / 1e9, 3), "unit": "Gcell-steps/s",
+                         "h2d_bytes_per_step": 3 * cells * esz, "d2h_bytes_per_step": nx * ny * esz,
+                         "ms_per_step": round(ems, 3),
+                         "what": "per step: J copied from pinned host, psatd_yee_step, one Ez plane read back"}
+        del host
+    if not args.skip_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"] = yee_cpu_sample(args.cpu_budget)
+    return result
+
+
+def yee_cpu_sample(budget_s: float):
+    """The FP64 Yee oracle on a 256 x 128 x 128 grid, repeated until the budget is spent."""
+    from oracle import yee_oracle as Y
+    from paper_1707_08500_gb300 import inputs as I
+    n = (256, 128, 128)
+    f = {k: v.numpy() for k, v in I.random_fields(n, 1707 + 61, names=Y.E_NAMES + Y.B_NAMES + ("Jx", "Jy", "Jz")).items()}
+    steps, t = 0, 0.0
+    while t < budget_s:
+        t0 = time.perf_counter()
+        f = Y.yee_step(f, (1.0, 1.0, 1.0), 0.5)
+        t += time.perf_counter() - t0
+        steps += 1
+    cells = n[0] * n[1] * n[2]
+    return {"value": cells * steps / t / 1e9, "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of a {n[0]}x{n[1]}x{n[2]} grid, {t:.1f} s"}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle, timed as it stands on the host cores."""
     from oracle import psatd_oracle as O
     from paper_1707_08500_gb300 import inputs as I
     if rank != 0:
         return None
+    if args.solver == "yee":
+        c = yee_cpu_sample(max(5.0, args.cpu_budget))
+        return {"impl": "reference", "metric": YEE_METRIC, "value": round(c["value"], 6), "unit": c["unit"],
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"yee-{args.workload}-grid (oracle on a bounded sample)"},
+                "cpu_baseline": c,
+                "e2e": {"value": round(c["value"], 6), "unit": c["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     wl = I.workload(args.workload)
     per_step = max(1, int(args.ref_subs))
     boxes = [(sd, {k: v.numpy() for k, v in I.box_fields(wl, sd, device="cpu").items()})
@@ -440,6 +560,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--grid-per-item", action="store_true", help="one CTA per work item instead of persistent grids")
     ap.add_argument("--accuracy-steps", type=int, default=0, help="also report FP32 batched vs FP64 plain after S steps")
+    ap.add_argument("--solver", choices=["psatd", "yee"], default="psatd",
+                    help="yee: the FDTD comparison solver on the workload's global grid")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -455,7 +577,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    out = run_ours(args, rank, world, local_rank)
+    out = run_yee(args, rank, world, local_rank) if args.solver == "yee" else run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -116,7 +116,8 @@ int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
                       const psatd_sub* subs, int32_t nsub, int32_t flags);
 
 /* Tunable launch shapes of a plan (0 = library default for every field).
- * chunk_b: (ky,kx) modes per CTA of the z/Eq. 1 stage, 1..64;
+ * chunk_b: (ky,kx) modes per CTA of the z/Eq. 1 stage, 1..1024 (reduced
+ * until the stage's tile fits in shared memory);
  * f1[3]: first factor of the two-stage FFT of the x (half length), y and z
  * axes; used for every subdomain whose length it divides with both factors
  * in 1..16, ignored otherwise. */

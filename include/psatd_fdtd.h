@@ -38,7 +38,8 @@ extern "C" {
  * Enqueued on `stream` (a cudaStream_t; NULL = legacy default stream);
  * returns before the step runs.  Allocates nothing.  Returns PSATD_OK,
  * PSATD_E_ARG (null or misaligned pointer, bad flags, overlap, bad c_dt/dx),
- * PSATD_E_SHAPE (an extent < 1 or a grid above 2^31 cells) or PSATD_E_CUDA
+ * PSATD_E_SHAPE (an extent < 1, a grid above 2^31 cells, Ny > 524280 or
+ * Nz > 2097120) or PSATD_E_CUDA
  * (launch failure). */
 int psatd_yee_step(const int32_t global_n[3], int32_t flags, double c_dt, const double dx[3],
                    const psatd_fields* in, const psatd_fields* out, void* stream);

@@ -292,7 +292,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     if (!out || !global_n || !subs || nsub <= 0) return PSATD_E_ARG;
     if (tuning) {
         const int cb = tuning->chunk_b;
-        if (cb < 0 || cb > 64) return PSATD_E_ARG;
+        if (cb < 0 || cb > 1024) return PSATD_E_ARG;
         for (int a = 0; a < 3; ++a) if (tuning->f1[a] < 0 || tuning->f1[a] > kMaxDft) return PSATD_E_ARG;
     }
     *out = nullptr;
@@ -435,8 +435,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
         int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
-        if (!(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 64 modes
-            while (M < 64 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 64 * 1024) M *= 2;
+        if (!(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 512 modes
+            while (M < 512 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 48 * 1024) M *= 2;
         while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
         d.chunkB = M;
         d.lgB = 0;

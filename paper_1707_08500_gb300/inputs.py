@@ -394,6 +394,18 @@ def laser_slab_box(wl: Workload, lo, shape, device) -> Dict[str, torch.Tensor]:
     return out
 
 
+def random_fields(global_n, seed: int, names=FIELD_NAMES[:9], device="cpu",
+                  dtype=torch.float64) -> Dict[str, torch.Tensor]:
+    """Independent U[-1, 1) values per cell for each named field, [Nz][Ny][Nx]
+    (one counter-based stream per field name)."""
+    nx, ny, nz = global_n
+    idx = torch.arange(nx * ny * nz, dtype=torch.int64, device=device)
+    out = {}
+    for i, n in enumerate(names):
+        out[n] = (2.0 * uniform(seed, 200 + FIELD_NAMES.index(n), idx) - 1.0).to(dtype).reshape(nz, ny, nx)
+    return out
+
+
 def global_fields(wl: Workload, device="cpu") -> Dict[str, torch.Tensor]:
     """All ten global fields, FP64, shaped [Nz][Ny][Nx]."""
     if wl.fields == "wavepacket":

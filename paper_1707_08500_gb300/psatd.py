@@ -33,7 +33,8 @@ STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NO
 EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
-           "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant")
+           "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
+           "psatd_yee_step", "psatd_yee_launches")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -176,6 +177,22 @@ def psatd_push_static(plan, c_dt: float, dx: Sequence[float], fields: FieldsT, g
 
 def psatd_exchange_guards(plan, fields: FieldsT, stream: Optional[int] = None):
     _check(lib().psatd_exchange_guards(plan, ctypes.byref(fields), ctypes.c_void_p(stream or 0)), plan)
+
+
+def psatd_yee_step(global_n: Sequence[int], flags: int, c_dt: float, dx: Sequence[float], fin: FieldsT,
+                   fout: FieldsT, stream: Optional[int] = None):
+    """One Yee FDTD step (Eqs. 2a/2b): fin = (E^n, B^{n-1/2}, J^{n+1/2}) ->
+    fout = (E^{n+1}, B^{n+1/2}); dense [Nz][Ny][Nx] device arrays."""
+    n = (ctypes.c_int32 * 3)(*global_n)
+    d = (ctypes.c_double * 3)(*dx)
+    _check(lib().psatd_yee_step(n, ctypes.c_int32(flags), ctypes.c_double(c_dt), d, ctypes.byref(fin),
+                                ctypes.byref(fout), ctypes.c_void_p(stream or 0)))
+
+
+def psatd_yee_launches() -> int:
+    v = ctypes.c_int32()
+    _check(lib().psatd_yee_launches(ctypes.byref(v)))
+    return v.value
 
 
 def psatd_destroy(plan):

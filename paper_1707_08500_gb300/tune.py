@@ -104,7 +104,7 @@ def autotune(wl: I.Workload, flags: int, device="cuda", reps: int = 3, use_cache
     # pass B: z split and chunk width
     bestB, bestT = None, None
     for fz in _divisor_splits(lens[2]):
-        for M in (2, 4, 6, 8, 12, 16):
+        for M in ((2, 4, 6, 8, 12, 16) if lens[2] >= 16 else (32, 64, 128, 256, 512)):
             cand = {"chunk_b": M, "f1": [0, 0, fz]}
             t = b.time(cand, reps)
             log.append(("B", cand, t))

@@ -22,7 +22,8 @@ def P():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "psatd.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(psatd_[a-z_]+)\s*\(", src)))
 
 
@@ -200,3 +201,38 @@ def test_split_plane_schedule_is_chosen_for_large_planes(P):
     with pytest.raises(P.PsatdError) as e:
         P.psatd_plan_create((1024, 256, 256), [I.Sub((0, 0, 0), (1024, 256, 256), 0, 0)], P.PSATD_F32)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("case", ["flags", "both", "shape", "dx", "null", "misaligned", "overlap_in", "overlap_out",
+                                  "too_tall"])
+def test_yee_step_rejects_bad_arguments(P, case):
+    """Argument checks of psatd_yee_step run before any CUDA call."""
+    n, flags, dx = [16, 16, 16], P.PSATD_F32, [1.0, 1.0, 1.0]
+    bytes_ = 16 * 16 * 16 * 4
+    base = 1 << 40
+    fin, fout = P.FieldsT(), P.FieldsT()
+    for a in range(3):
+        fin.E[a], fin.B[a], fin.J[a] = base + a * bytes_, base + (3 + a) * bytes_, base + (6 + a) * bytes_
+        fout.E[a], fout.B[a] = base + (9 + a) * bytes_, base + (12 + a) * bytes_
+    if case == "flags":
+        flags |= P.PSATD_STAGGERED
+    elif case == "both":
+        flags = P.PSATD_F32 | P.PSATD_F64
+    elif case == "shape":
+        n[1] = 0
+    elif case == "dx":
+        dx[2] = -1.0
+    elif case == "null":
+        fin.J[2] = None
+    elif case == "misaligned":
+        fout.B[1] += 4
+    elif case == "overlap_in":
+        fout.E[0] = fin.B[2] + 64
+    elif case == "overlap_out":
+        fout.B[2] = fout.E[1]
+    elif case == "too_tall":
+        n = [1, 1 << 20, 1]
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_yee_step(n, flags, 0.5, dx, fin, fout)
+    assert e.value.code == (-2 if case in ("shape", "too_tall") else -1)
+    assert P.psatd_yee_launches() == 1
