@@ -69,6 +69,22 @@ extern "C" {
                                      default persistent grid (as many CTAs as
                                      fit on the GPU, drawing work items from a
                                      counter in the workspace)                   */
+#define PSATD_HEAT           0x100 /* the local-FFT heat equation instead of
+                                     Maxwell (Sec. 5: the decomposition applies
+                                     to other initial-value problems; the
+                                     paper names the heat equation).  One scalar
+                                     field T in fields->E[0] is advanced per
+                                     step by the exact per-mode solution of
+                                     dT/dt = D lap T + Q:
+                                       T~' = exp(-x) T~ + (1-exp(-x))/x S~,
+                                       x = D dt sum_u [k_u]^2,
+                                     with [k_u] the order-p staggered modified
+                                     wavenumber (p = 0: exact k; the Nyquist
+                                     index keeps k = pi/du) and S = Q dt the
+                                     heat added per cell over the step.  Not
+                                     with PSATD_STAGGERED or PSATD_GAUSS_DIAG. */
+#define PSATD_HEAT_SOURCE    0x200 /* with PSATD_HEAT: a source S in
+                                     fields->J[0] (read only)                   */
 #define PSATD_SPLIT_PLANES   0x80 /* split-plane schedule: the x and y transforms
                                      of the forward and inverse plane stages run
                                      as separate row and column launches (five
@@ -152,6 +168,8 @@ int psatd_set_workspace(psatd_plan_t plan, void* dev_ptr, size_t bytes);
  * to the workspace (rounded to FP32 for PSATD_F32).  Tables are shared by all
  * subdomains with the same local shape and order.  Requires the workspace. */
 int psatd_set_coeffs(psatd_plan_t plan, double c_dt, const double dx[3]);
+/* For PSATD_HEAT plans the scalar argument is D*dt instead of c*dt, and the
+ * tables hold exp(-x) and (1-exp(-x))/x per mode. */
 
 /* One PSATD step of every subdomain (Sec. 3.2 with Eq. 1), followed by the
  * guard replacement (Fig. 3 step 3), enqueued on `stream` (a cudaStream_t;
@@ -163,6 +181,9 @@ int psatd_set_coeffs(psatd_plan_t plan, double c_dt, const double dx[3]);
  * spectrum of its padded box (unnormalised transforms); requires
  * PSATD_GAUSS_DIAG. */
 int psatd_push(psatd_plan_t plan, const psatd_fields* fields, double* gauss_dev, void* stream);
+/* PSATD_HEAT plans: the same step for the scalar T (fields->E[0], updated in
+ * place, guards included) with the optional source fields->J[0]; every other
+ * pointer of `fields` is ignored and gauss_dev must be NULL. */
 
 /* psatd_push that also records caller-created CUDA events on `stream` at the
  * stage boundaries of the batched schedule: events[0] before pass A (forward
@@ -204,7 +225,8 @@ int psatd_push_static(psatd_plan_t plan, double c_dt, const double dx[3], const 
                       double* gauss_dev, void* stream);
 
 /* Copy every valid cell into each guard cell that images it (all 26
- * neighbour directions, periodic wrap), for E and B only, on `stream`. */
+ * neighbour directions, periodic wrap), for E and B only (T only for
+ * PSATD_HEAT plans), on `stream`. */
 int psatd_exchange_guards(psatd_plan_t plan, const psatd_fields* fields, void* stream);
 
 /* Release the plan's host memory (the workspace stays the caller's). */
