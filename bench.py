@@ -106,7 +106,7 @@ def replica_value(valid_cells: int, world: int, ms_per_step: float) -> float:
     return valid_cells * world / (ms_per_step / 1e3) / 1e9
 
 
-def stage_bytes(wl, nf: int, esz: int):
+def stage_bytes(wl, nf: int, esz: int, nout: int = 6):
     """Algorithmic HBM bytes per launch of each stage (unique inputs + outputs):
     A reads nf real fields and writes nf half spectra; B reads nf spectra and
     writes 6 spectra on the valid z planes; C reads those and writes 6 real
@@ -119,8 +119,8 @@ def stage_bytes(wl, nf: int, esz: int):
         spec = lz * ly * (lx // 2 + 1) * 2 * esz
         vspec = sd.n[2] * ly * (lx // 2 + 1) * 2 * esz
         A += nf * (cells * esz + spec)
-        B += nf * spec + 6 * vspec
-        C += 6 * (vspec + cells * esz)
+        B += nf * spec + nout * vspec
+        C += nout * (vspec + cells * esz)
         local += cells
     return {"A": A, "B": B, "C": C}, local
 
@@ -483,6 +483,103 @@ def run_yee(args, rank, world, local_rank):
     return result
 
 
+HEAT_METRIC = "Gcell-steps/s of the local-FFT heat-equation step (exact per-mode decay), FP32; % HBM roof"
+
+
+def run_heat(args, rank, world, local_rank):
+    """The local-FFT heat equation (PSATD_HEAT) with a source on the
+    workload's decomposition: the same three stages with one field out (two
+    in).  D dt = 0.5 cell^2."""
+    import torch
+    from paper_1707_08500_gb300 import build as B
+    from paper_1707_08500_gb300 import inputs as I
+    from paper_1707_08500_gb300 import psatd as P
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = I.workload(args.workload)
+    prec = args.precision or "f32"
+    esz = 4 if prec == "f32" else 8
+    d_dt = 0.5
+    sol = P.HeatSolver(wl, d_dt, source=True, precision=prec, device=dev)
+    g = I.random_fields(wl.global_n, 1707 + 72, names=("Jx", "Jy"), device=dev)
+    sol.load_global({"T": g["Jx"], "S": 0.01 * g["Jy"]}, names=("T", "S"), guards=True)
+    del g
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def mkev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+    for _ in range(args.warmup):
+        sol.push(sp)
+    torch.cuda.synchronize()
+    evs = [[mkev() for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    t0, t1 = mkev(), mkev()
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(args.steps):
+            P.psatd_push_profiled(sol.plan, sol.fields, None, sp, [e.cuda_event for e in evs[k]])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev) / args.steps
+    stage_ms = {st: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
+                for i, st in enumerate("ABC")}
+    by, local = stage_bytes(wl, 2, esz, nout=1)
+    peak, peak_kind = _peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    names = {"A": "k_pass_a", "B": "k_pass_b_heat", "C": "k_pass_c"}
+    achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
+    valid = wl.valid_cells
+    result = {
+        "metric": HEAT_METRIC, "value": round(replica_value(valid, world, ms), 4), "unit": "Gcell-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": f"heat-{wl.name}", "global_n": list(wl.global_n), "subdomains": len(wl.subs),
+                   "local_n": list(wl.subs[0].local), "guards": wl.subs[0].ng, "order": wl.subs[0].p, "d_dt": d_dt,
+                   "source": True, "l2": f"inputs ({local * 2 * esz / 1e9:.1f} GB) larger than L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "stages": {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
+                        "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"},
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind},
+        "step_roofline": {"three_pass_bytes_per_step": sum(by.values()),
+                          "frac_three_pass": round(sum(by.values()) / (ms / 1e3) / 1e9 / peak, 4)},
+        "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
+        "clocks": clk.summary(),
+    }
+    if not args.skip_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"] = heat_cpu_sample(wl, args.cpu_budget)
+    return result
+
+
+def heat_cpu_sample(wl, budget_s: float):
+    """The FP64 heat oracle on whole subdomain steps until the budget is spent."""
+    from oracle import heat_oracle as H
+    import numpy as np
+    rng = np.random.default_rng(1)
+    t_used, cells, nsub = 0.0, 0, 0
+    for sd in wl.subs[:: max(1, len(wl.subs) // 64)]:
+        lx, ly, lz = sd.local
+        T, S = rng.standard_normal((lz, ly, lx)), rng.standard_normal((lz, ly, lx))
+        t0 = time.perf_counter()
+        H.local_heat_push(T, S, sd.local, wl.dx, sd.p, 0.5)
+        t_used += time.perf_counter() - t0
+        cells += sd.n[0] * sd.n[1] * sd.n[2]
+        nsub += 1
+        if t_used > budget_s:
+            break
+    from oracle import psatd_oracle as O
+    return {"value": cells / t_used / 1e9, "unit": "Gcell-steps/s", "cores": O.WORKERS, "kind": "oracle",
+            "sample": f"{nsub} of {len(wl.subs)} subdomain steps ({cells} valid cells), {t_used:.1f} s"}
+
+
 def yee_cpu_sample(budget_s: float):
     """The FP64 Yee oracle on a 256 x 128 x 128 grid, repeated until the budget is spent."""
     from oracle import yee_oracle as Y
@@ -506,6 +603,14 @@ def run_reference(args, rank, world):
     from paper_1707_08500_gb300 import inputs as I
     if rank != 0:
         return None
+    if args.solver == "heat":
+        c = heat_cpu_sample(I.workload(args.workload), max(5.0, args.cpu_budget))
+        return {"impl": "reference", "metric": HEAT_METRIC, "value": round(c["value"], 6), "unit": c["unit"],
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"heat-{args.workload} (oracle on a bounded sample)"},
+                "cpu_baseline": c,
+                "e2e": {"value": round(c["value"], 6), "unit": c["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.solver == "yee":
         c = yee_cpu_sample(max(5.0, args.cpu_budget))
         return {"impl": "reference", "metric": YEE_METRIC, "value": round(c["value"], 6), "unit": c["unit"],
@@ -560,8 +665,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--grid-per-item", action="store_true", help="one CTA per work item instead of persistent grids")
     ap.add_argument("--accuracy-steps", type=int, default=0, help="also report FP32 batched vs FP64 plain after S steps")
-    ap.add_argument("--solver", choices=["psatd", "yee"], default="psatd",
-                    help="yee: the FDTD comparison solver on the workload's global grid")
+    ap.add_argument("--solver", choices=["psatd", "yee", "heat"], default="psatd",
+                    help="yee: the FDTD comparison solver on the workload's global grid; "
+                         "heat: the local-FFT heat equation on the workload's decomposition")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -577,7 +683,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    out = run_yee(args, rank, world, local_rank) if args.solver == "yee" else run_ours(args, rank, world, local_rank)
+    runner = {"yee": run_yee, "heat": run_heat}.get(args.solver, run_ours)
+    out = runner(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -98,6 +98,7 @@ struct LaunchCommon {
     unsigned long long* work;   // persistent-launch work counter (in the workspace)
     int persistent;             // 1: persistent grids drawing tickets; 0: one CTA per work item
     int nsub, nseg, nf, staggered, own_only;
+    int nout;             // output fields written by the inverse stages: 6 (E, B) or 1 (heat: T)
     int64_t per_sub[5];   // items per subdomain of passes A, B, C and of the split schedule's column stages
                           // (forward, inverse) when every subdomain has the same shape, else 0
     int variant;          // index into kFixedF32 / kFixedF64, or -1 for the descriptor-driven kernels

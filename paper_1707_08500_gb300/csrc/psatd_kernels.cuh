@@ -84,7 +84,8 @@ struct Args {
     int64_t item0, nitems;  // items handled by this launch
     int64_t per_sub[5];     // items per subdomain of each stage when uniform, else 0
     int nsub, nseg;
-    int nf;                 // fields transformed forward (9, or 10 with rho)
+    int nf;                 // fields transformed forward (9, or 10 with rho; heat: 1, or 2 with a source)
+    int nout;               // fields written back (6; heat: 1)
     int staggered;
     int own_only;           // pass C writes only the own valid box
 };
@@ -262,7 +263,8 @@ __device__ __forceinline__ void split_pair(int i, int h, int f2, int& pa, int& p
 
 // Stages: 0 = pass A, 1 = pass B, 2 = pass C, 3 = standalone exchange; the
 // split-plane schedule replaces A by 4 (x rows) + 5 (y columns) and C by
-// 6 (y columns) + 7 (x rows and the exchange scatter).
+// 6 (y columns) + 7 (x rows and the exchange scatter); 8 is pass B of the
+// heat equation (its items are those of pass B).
 template <int STAGE>
 __device__ __forceinline__ int64_t stage_item(const SubDesc& d) {
     return STAGE == 0 || STAGE == 4 ? d.itemA : STAGE == 1 ? d.itemB : STAGE == 5 ? d.itemA2
@@ -586,6 +588,62 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
     }
 }
 
+
+// ---- pass B of the heat equation: z transforms and the exact decay ----------
+// Same chunking as pass B.  Per mode T~' = A T~ + B S~ with A = exp(-x) and
+// B = (1 - exp(-x))/x, x = D dt |[k]|^2 (both scaled by 1/(Lx Ly Lz)), read
+// from the first two coefficient arrays; S is the optional source (field 1).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass_b_heat(Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+    __shared__ SubDesc d;
+    __shared__ int64_t s_ticket[2];
+    Tickets<T> tk(a, s_ticket);
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
+        decode_item<1>(a, it, &d);
+        const GeoDyn g(d);
+        const int Lz = g.Lz, M = g.M, lgM = g.lgM, Q = g.q;
+        const int q0 = int(it - d.itemB) * M;
+        const int mc = min(M, Q - q0);
+        const int nf = a.nf, fs = g.fs;
+        cpx<T>* spec = a.spec + d.spec_off;
+        for (int f = 0; f < nf; ++f) {
+            const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
+            cpx<T>* s = sm + f * fs;
+            loop2(M, Lz, [&](int z, int m) {
+                const cpx<T>* gp = src + int64_t(z) * Q + (m < mc ? m : 0);
+                if constexpr (sizeof(T) == 4) cp_async8z(s + z * M + m, gp, m < mc ? 8 : 0);
+                else cp_async16(s + z * M + m, gp, m < mc ? 16 : 0);
+            });
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        fft_fwd<true>(sm, g.az, Batch{nf * M, 1, lgM, fs, M, M}, a.tw);
+        const int64_t NM = int64_t(Lz) * Q;
+        loop2(M, Lz, [&](int zp, int m) {
+            if (m >= mc) return;
+            const T* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q0 + m;
+            cpx<T>* p = sm + zp * M + m;
+            cpx<T> v = scale(p[0], __ldg(tb));
+            if (nf > 1) v = v + scale(p[fs], __ldg(tb + NM));
+            p[0] = v;
+        });
+        __syncthreads();
+        fft_inv<true>(sm, g.az, Batch{M, 1, lgM, fs, M, M}, a.tw);
+        {
+            const int ngz = g.ngz, nz = g.nvz;
+            cpx<T>* dst = spec + int64_t(ngz) * Q + q0;
+            const cpx<T>* s = sm + ngz * M;
+            loop2(M, nz, [&](int zv, int m) {
+                if (m < mc) stcs_c(dst + int64_t(zv) * Q + m, s[zv * M + m]);
+            });
+        }
+        __syncthreads();
+    }
+}
+
 // ---- pass C: inverse y and x transforms, fused guard replacement ------------
 template <typename T, class G>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k_pass_c(Args<T> a) {
@@ -801,7 +859,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange(Args<T> a) {
         const Segment& sg = a.segs[lo];
         const SubDesc& sd = a.subs[sg.src];
         const int z = sg.z0 + int(it - sg.item);
-        for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < a.nout; ++f) {
             T* fld = a.eb[f];
             const T* src = fld + sd.field_off + (int64_t(z) * sd.L[1] + sg.y0) * sd.L[0] + sg.x0;
             T* dst = fld + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
@@ -851,6 +909,7 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     a.nsub = c.nsub;
     a.nseg = c.nseg;
     a.nf = c.nf;
+    a.nout = c.nout;
     a.staggered = c.staggered;
     a.own_only = c.own_only;
     return a;
@@ -897,6 +956,7 @@ static cudaError_t launch_geo(int stage, const Args<T>& a, int smem, cudaStream_
         case 5: return launch_kernel<T>(k_cols<T, false>, a, smem, st);
         case 6: return launch_kernel<T>(k_cols<T, true>, a, smem, st);
         case 7: return launch_kernel<T>(k_rows_inv<T>, a, smem, st);
+        case 8: return launch_kernel<T>(k_pass_b_heat<T>, a, smem, st);
         default: return launch_kernel<T>(k_exchange<T>, a, 0, st);
     }
 }

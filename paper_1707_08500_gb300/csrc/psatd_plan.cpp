@@ -96,6 +96,17 @@ double kmod(int i, int L, double du, int p, bool stag) {
     return s;
 }
 
+// [k] of the heat-equation Laplacian symbol: the order-p staggered first
+// difference (p = 0: exact k), the Nyquist index keeping k = -pi/du
+double kheat(int i, int L, double du, int p) {
+    const double k = kexact(i, L, du);
+    if (p == 0) return k;
+    const std::vector<double> c = weights_staggered(p);
+    double s = 0;
+    for (size_t j = 0; j < c.size(); ++j) s += c[j] * 2.0 * std::sin((2.0 * j + 1.0) * k * du / 2) / du;
+    return s;
+}
+
 bool factor(int n, int& f1, int& f2) {
     f1 = split_first(n);   // the most balanced split with both factors in 1..16
     if (!f1) return false;
@@ -116,6 +127,8 @@ struct psatd_plan_s {
     int64_t arena_elems = 0;
     int nf = 9;
     bool f64 = false, stag = false, plain = false, diag = false;
+    bool heat = false, heat_src = false;   // the heat equation (Sec. 5) instead of Maxwell
+    int nout = 6;                          // fields written back: E, B (heat: T)
     // twiddle pool: (n) -> offset; post twiddles: (Lx) -> offset
     std::map<int, int> tw_off, post_off;
     int64_t n_tw = 0;
@@ -228,6 +241,27 @@ static void table_images(const psatd_plan_s* p, double c_dt, const double dx[3],
         const double invN = 1.0 / (double(L[0]) * L[1] * L[2]);
         const int64_t NM = int64_t(L[2]) * q;
         double* tc = tab.data() + p->tab_coef_off[ti];
+        if (p->heat) {
+            // heat equation: exp(-x) and (1 - exp(-x))/x, x = D dt |[k]|^2
+            // (c_dt holds D dt), scaled by 1/(Lx Ly Lz)
+            std::vector<double> k2[3];
+            for (int a = 0; a < 3; ++a) {
+                k2[a].resize(nat[a].size());
+                for (size_t P = 0; P < nat[a].size(); ++P) {
+                    const double v = kheat(nat[a][P], L[a], dx[a], key.p);
+                    k2[a][P] = v * v;
+                }
+            }
+            for (int zp = 0; zp < L[2]; ++zp)
+                for (int yp = 0; yp < L[1]; ++yp)
+                    for (int xp = 0; xp < lxh; ++xp) {
+                        const double x = c_dt * (k2[0][xp] + k2[1][yp] + k2[2][zp]);
+                        const int64_t i = int64_t(zp) * q + int64_t(yp) * lxh + xp;
+                        tc[TAB_C * NM + i] = std::exp(-x) * invN;
+                        tc[TAB_S * NM + i] = (x > 0 ? -std::expm1(-x) / x : 1.0) * invN;
+                    }
+            continue;
+        }
         for (int zp = 0; zp < L[2]; ++zp)
             for (int yp = 0; yp < L[1]; ++yp)
                 for (int xp = 0; xp < lxh; ++xp) {
@@ -301,7 +335,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     auto bad = [&](int code, const std::string& m) { int c = fail(p, code, m); delete p; return c; };
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
-    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D | PSATD_SPLIT_PLANES))
+    if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D |
+                  PSATD_SPLIT_PLANES | PSATD_HEAT | PSATD_HEAT_SOURCE))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -309,6 +344,14 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     p->plain = flags & PSATD_PLAIN;
     p->diag = flags & PSATD_GAUSS_DIAG;
     p->nf = p->diag ? 10 : 9;
+    p->heat = flags & PSATD_HEAT;
+    p->heat_src = flags & PSATD_HEAT_SOURCE;
+    if (p->heat_src && !p->heat) return bad(PSATD_E_ARG, "PSATD_HEAT_SOURCE needs PSATD_HEAT");
+    if (p->heat && (p->stag || p->diag)) return bad(PSATD_E_ARG, "PSATD_HEAT excludes PSATD_STAGGERED and PSATD_GAUSS_DIAG");
+    if (p->heat) {
+        p->nf = p->heat_src ? 2 : 1;
+        p->nout = 1;
+    }
     for (int a = 0; a < 3; ++a) {
         if (global_n[a] <= 0) return bad(PSATD_E_SHAPE, "global extents must be positive");
         p->gn[a] = global_n[a];
@@ -437,6 +480,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
         if (!(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 512 modes
             while (M < 512 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 48 * 1024) M *= 2;
+        if (!(tuning && tuning->chunk_b) && p->heat)       // one or two fields: wider chunks
+            while (M < 64 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 32 * 1024) M *= 2;
         while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
         d.chunkB = M;
         d.lgB = 0;
@@ -471,13 +516,13 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
             const int64_t cb = (d.lxh + d.cols - 1) / d.cols;
             iA += int64_t(p->nf) * d.L[2] * rb_in;
             iA2 += int64_t(p->nf) * d.L[2] * cb;
-            iC1 += 6 * int64_t(d.nv[2]) * cb;
-            iC += 6 * int64_t(d.nv[2]) * rb_out;
+            iC1 += int64_t(p->nout) * d.nv[2] * cb;
+            iC += int64_t(p->nout) * d.nv[2] * rb_out;
             p->smemR = std::max(p->smemR, d.rows * d.pitch * csz);
             p->smemK = std::max(p->smemK, d.L[1] * d.cols * csz);
         } else {
             iA += int64_t(p->nf) * d.L[2];
-            iC += 6 * int64_t(d.nv[2]);
+            iC += int64_t(p->nout) * d.nv[2];
         }
         iB += (d.q + d.chunkB - 1) / d.chunkB;
     }
@@ -653,6 +698,12 @@ int psatd_set_coeffs(psatd_plan_t p, double c_dt, const double dx[3]) {
 
 static int check_fields(psatd_plan_s* p, const psatd_fields* f, bool need_j) {
     if (!f) return fail(p, PSATD_E_ARG, "null fields");
+    if (p->heat) {
+        if (!f->E[0] || reinterpret_cast<uintptr_t>(f->E[0]) % 16) return fail(p, PSATD_E_ARG, "T (fields->E[0]) must be a 16-byte aligned arena");
+        if (need_j && p->heat_src && (!f->J[0] || reinterpret_cast<uintptr_t>(f->J[0]) % 16))
+            return fail(p, PSATD_E_ARG, "PSATD_HEAT_SOURCE needs a 16-byte aligned source arena in fields->J[0]");
+        return PSATD_OK;
+    }
     for (int a = 0; a < 3; ++a) {
         if (!f->E[a] || !f->B[a]) return fail(p, PSATD_E_ARG, "null E or B arena");
         if (need_j && !f->J[a]) return fail(p, PSATD_E_ARG, "null J arena");
@@ -678,12 +729,21 @@ static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f
     c.spec = base + p->off_spec;
     for (int a = 0; a < 3; ++a) { c.eb[a] = f->E[a]; c.eb[3 + a] = f->B[a]; c.jr[a] = f->J[a]; }
     c.jr[3] = f->rho;
+    if (p->heat) {
+        // the heat equation's inputs are field 0 (T, written back) and field 1
+        // (the source, read by the forward stages only)
+        for (int a = 0; a < 6; ++a) c.eb[a] = nullptr;
+        for (int a = 0; a < 4; ++a) c.jr[a] = nullptr;
+        c.eb[0] = f->E[0];
+        c.eb[1] = p->heat_src ? const_cast<void*>(f->J[0]) : nullptr;   // never written (nout = 1)
+    }
     c.gauss_part = reinterpret_cast<double*>(base + p->off_gauss);
     c.work = reinterpret_cast<unsigned long long*>(base + p->off_work);
     c.persistent = (p->flags & PSATD_GRID_PER_ITEM) ? 0 : 1;
     c.nsub = int(p->desc.size());
     c.nseg = int(p->segs.size());
     c.nf = p->nf;
+    c.nout = p->nout;
     c.staggered = p->stag ? 1 : 0;
     c.own_only = 0;
     for (int i = 0; i < 5; ++i) c.per_sub[i] = p->per_sub[i];
@@ -738,7 +798,7 @@ static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaS
             if ((e = stage(p, 5, c, r.a20, r.a2n, p->smemK, s)) != cudaSuccess) return cuda_fail(p, e, "y columns launch");
         }
         if (!p->plain && (e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
-        if ((e = stage(p, 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        if ((e = stage(p, p->heat ? 8 : 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
         if (!p->plain && (e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
         if (!p->split) {
             if ((e = stage(p, 2, c, r.c0, r.cn, p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");

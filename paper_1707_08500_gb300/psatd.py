@@ -26,6 +26,8 @@ PSATD_PLAIN = 0x10
 PSATD_GRID_PER_ITEM = 0x20
 PSATD_2D = 0x40
 PSATD_SPLIT_PLANES = 0x80
+PSATD_HEAT = 0x100
+PSATD_HEAT_SOURCE = 0x200
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}
@@ -335,3 +337,39 @@ class Solver:
 
     def gauss_sums(self):
         return self.gauss_out.view(-1, 2).cpu().numpy()
+
+
+class HeatSolver(Solver):
+    """The local-FFT heat equation (PSATD_HEAT) on the decomposition of a
+    workload: arenas "T" (advanced in place, guards included) and, with a
+    source, "S" (heat added per cell over a step).  d_dt = D dt."""
+
+    def __init__(self, wl: "_inputs.Workload", d_dt: float, source: bool = False, precision: Optional[str] = None,
+                 plain: bool = False, device="cuda", tuning: Optional[dict] = None, extra_flags: int = 0):
+        self.wl = wl
+        self.precision = precision or wl.precision
+        self.dtype = torch.float64 if self.precision == "f64" else torch.float32
+        flags = (PSATD_F64 if self.precision == "f64" else PSATD_F32) | PSATD_HEAT
+        if source:
+            flags |= PSATD_HEAT_SOURCE
+        if wl.two_d:
+            flags |= PSATD_2D
+        if plain:
+            flags |= PSATD_PLAIN
+        flags |= extra_flags
+        self.flags, self.gauss, self.device, self.tuning = flags, False, torch.device(device), tuning
+        self.gauss_out = None
+        self.plan = psatd_plan_create(wl.global_n, wl.subs, flags, tuning)
+        self.layout = [psatd_layout(self.plan, s) for s in range(len(wl.subs))]
+        self.arena_elems = psatd_arena_elems(self.plan)
+        self.ws_bytes = psatd_workspace_bytes(self.plan)
+        names = ("T", "S") if source else ("T",)
+        self.arenas = {n: torch.zeros(self.arena_elems, dtype=self.dtype, device=self.device) for n in names}
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        psatd_set_workspace(self.plan, self.ws_ptr, self.ws_bytes)
+        psatd_set_coeffs(self.plan, d_dt, wl.dx)
+        f = FieldsT()
+        f.E[0] = self.arenas["T"].data_ptr()
+        f.J[0] = self.arenas["S"].data_ptr() if source else None
+        self.fields = f

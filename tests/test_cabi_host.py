@@ -236,3 +236,26 @@ def test_yee_step_rejects_bad_arguments(P, case):
         P.psatd_yee_step(n, flags, 0.5, dx, fin, fout)
     assert e.value.code == (-2 if case in ("shape", "too_tall") else -1)
     assert P.psatd_yee_launches() == 1
+
+
+def test_heat_plans(P):
+    """PSATD_HEAT: one field in (two with a source), one out; the Maxwell-only
+    flags are rejected."""
+    g = (32, 32, 32)
+    subs = I.tensor_decomposition([16, 16], [32], [32], 4, 8)
+    for flags in (P.PSATD_F32 | P.PSATD_HEAT, P.PSATD_F64 | P.PSATD_HEAT | P.PSATD_HEAT_SOURCE,
+                  P.PSATD_F32 | P.PSATD_HEAT | P.PSATD_PLAIN, P.PSATD_F32 | P.PSATD_HEAT | P.PSATD_SPLIT_PLANES):
+        h = P.psatd_plan_create(g, subs, flags)
+        try:
+            assert P.psatd_layout(h, 0)[1] == (24, 40, 40)
+            maxwell = P.psatd_plan_create(g, subs, flags & ~(P.PSATD_HEAT | P.PSATD_HEAT_SOURCE))
+            assert P.psatd_workspace_bytes(h) < P.psatd_workspace_bytes(maxwell)
+            assert P.psatd_push_launches(h) == P.psatd_push_launches(maxwell)
+            P.psatd_destroy(maxwell)
+        finally:
+            P.psatd_destroy(h)
+    for flags in (P.PSATD_F32 | P.PSATD_HEAT_SOURCE, P.PSATD_F32 | P.PSATD_HEAT | P.PSATD_STAGGERED,
+                  P.PSATD_F32 | P.PSATD_HEAT | P.PSATD_GAUSS_DIAG):
+        with pytest.raises(P.PsatdError) as e:
+            P.psatd_plan_create(g, subs, flags)
+        assert e.value.code == -1
