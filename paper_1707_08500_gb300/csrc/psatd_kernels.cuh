@@ -91,6 +91,9 @@ struct Args {
 };
 
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T> struct vec2;
 template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
@@ -140,6 +143,9 @@ __device__ __forceinline__ void cp_async8z(void* dst, const void* src, int src_b
                  :: "r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src)), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // one complex value
 template <typename T>
 __device__ __forceinline__ void cp_async_c(cpx<T>* dst, const cpx<T>* src) {
@@ -451,13 +457,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k
 }
 
 // ---- pass B: z transforms and the Eq. 1 update -----------------------------
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// Sum of v over the CTA (a pairwise tree, in T), returned to thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) red[w] = v;
     __syncthreads();
-    double s = 0;
+    T s = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < kThreads / 32; ++i) s += red[i];
     }
@@ -470,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
-    __shared__ double red[2][kThreads / 32];
+    __shared__ T red[2][kThreads / 32];
     __shared__ int64_t s_ticket[2];
     Tickets<T> tk(a, s_ticket);
     for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
@@ -502,15 +510,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
                     else cp_async16(s + z * M + m, g, m < mc ? 16 : 0);
                 });
             }
+            if (f == 5) cp_async_commit();          // E and B: the first group
         }
+        cp_async_commit();                          // J (and rho): the second group
+        // transform E and B while J and rho are still arriving
+        cp_async_wait_one();
+        __syncthreads();
+        fft_fwd<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
         cp_async_wait_all();
         __syncthreads();
-        fft_fwd<true>(sm, g.az, Batch{nf * M, 1, lgM, fs, M, M}, a.tw);
+        fft_fwd<true>(sm + 6 * fs, g.az, Batch{(nf - 6) * M, 1, lgM, fs, M, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
         const T* __restrict__ tk = a.tab + d.tab_k;
         const T Nfull = T(double(Lx) * double(Ly) * double(Lz));
-        double g_res = 0.0, g_rho = 0.0;
+        // Gauss partial sums in the stage's precision (FP64 throughput is a
+        // small fraction of FP32 on this part); one FMA forms the residual
+        // with a single rounding; the per-item sums are accumulated in FP64
+        // by the reduction kernel
+        T g_res = T(0), g_rho = T(0);
         loop2(M, Lz, [&](int zp, int m) {
             if (m >= mc) return;
             const int q = q0 + m;
@@ -552,11 +570,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
                 // Gauss residual i[k].E' - rho on the unnormalised spectrum
                 const cpx<T> rho = p[9 * fs];
                 const cpx<T> div = mul_i(scale(F0, kx) + scale(F1, ky) + scale(F2, kz));
-                const double rx = double(div.x) * double(Nfull) - double(rho.x);
-                const double ry = double(div.y) * double(Nfull) - double(rho.y);
-                const double wgt = (xp == 0 || xp == lxh - 1) ? 1.0 : 2.0;
+                const T rx = fma_t(div.x, Nfull, -rho.x);
+                const T ry = fma_t(div.y, Nfull, -rho.y);
+                const T wgt = (xp == 0 || xp == lxh - 1) ? T(1) : T(2);
                 g_res += wgt * (rx * rx + ry * ry);
-                g_rho += wgt * (double(rho.x) * double(rho.x) + double(rho.y) * double(rho.y));
+                g_rho += wgt * (rho.x * rho.x + rho.y * rho.y);
             }
             if (a.staggered) {
                 const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
@@ -577,8 +595,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
             });
         }
         if (nf > 9) {
-            const double s1 = block_sum(g_res, red[0]);
-            const double s2 = block_sum(g_rho, red[1]);
+            const double s1 = double(block_sum(g_res, red[0]));
+            const double s2 = double(block_sum(g_rho, red[1]));
             if (threadIdx.x == 0) {
                 a.gauss_part[2 * it] = s1;
                 a.gauss_part[2 * it + 1] = s2;
