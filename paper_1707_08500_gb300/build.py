@@ -48,7 +48,8 @@ def _compile(src: str, extra, verbose) -> str:
 
 def build(verbose: bool = False, extra=(), force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "psatd.h")]
+    inc = os.path.join(ROOT, "include")
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) > max(os.path.getmtime(d) for d in deps):
         return LIB
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:

@@ -32,6 +32,9 @@
 #ifndef PSATD_MINB_A
 #define PSATD_MINB_A 5
 #endif
+#ifndef PSATD_MINB_A_FIXED
+#define PSATD_MINB_A_FIXED 6    // compile-time geometry: fewer registers live, one more CTA fits
+#endif
 #ifndef PSATD_MINB_B
 #define PSATD_MINB_B 4
 #endif
@@ -401,6 +404,7 @@ struct Tickets {
 // with NG guards (GeoFix), in which case every stride, loop bound and DFT size
 // below is a constant.
 struct GeoDyn {
+    static constexpr bool kFixed = false;
     int Lx, Ly, Lz, h, lxh, pitch, q, ng, ngz, nvy, nvz, M, lgM, fs;
     AxisPlan ax, ay, az;
     __device__ explicit GeoDyn(const SubDesc& d)
@@ -410,6 +414,7 @@ struct GeoDyn {
 
 template <int L, int NG, int MB, int CSZ>
 struct GeoFix {
+    static constexpr bool kFixed = true;
     static constexpr int Lx = L, Ly = L, Lz = L, h = L / 2, lxh = L / 2 + 1, pitch = (L / 2 + 1) | 1;
     static constexpr int q = L * (L / 2 + 1), ng = NG, ngz = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
     static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
@@ -422,7 +427,8 @@ struct GeoFix {
 
 // ---- pass A: x (real) and y forward transforms of one plane ---------------
 template <typename T, class G>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_A : 2) k_pass_a(Args<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (G::kFixed ? PSATD_MINB_A_FIXED : PSATD_MINB_A) : 2)
+k_pass_a(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
