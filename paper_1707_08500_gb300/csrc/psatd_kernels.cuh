@@ -27,6 +27,8 @@
 #include "psatd_internal.h"
 #include "small_dft.cuh"
 
+#include <mutex>
+
 // Minimum resident CTAs per SM requested from the compiler for each stage
 // kernel (FP32; FP64 uses 2), which caps its registers per thread.
 #ifndef PSATD_MINB_A
@@ -376,24 +378,33 @@ __device__ __forceinline__ const T* field_in(const Args<T>& a, int f) {
 }
 
 // Work loop of the stage kernels.  Persistent launches: each CTA draws the
-// next unprocessed item of the launch from a global ticket counter (zeroed by
-// the host before the launch) until every item is taken; the ticket for the
-// following item is drawn at the start of the current one, into the other of
-// two shared slots, so no CTA waits on the atomic between items.  Otherwise
-// CTA b processes item item0 + b only.  Every loop body ends with
-// __syncthreads(), which orders the slot writes and reads.
+// next unprocessed item of the launch from a global ticket counter until
+// every item is taken; the ticket for the following item is drawn at the
+// start of the current one, into the other of two shared slots, so no CTA
+// waits on the atomic between items.  Every CTA stops after drawing exactly
+// one ticket past the last item, so a launch draws nitems + gridDim.x tickets
+// in all; the CTA that draws the last of them returns the counter to zero for
+// the next launch on the stream (the counter starts at zero when the
+// workspace is attached).  Otherwise CTA b processes item item0 + b only.
+// Every loop body ends with __syncthreads(), which orders the slot writes and
+// reads.
 template <typename T>
 struct Tickets {
     const Args<T>& a;
     int64_t* slot;
     int par = 0;
+    __device__ int64_t draw() const {
+        const int64_t k = int64_t(atomicAdd(a.work, 1ull));
+        if (k == a.nitems + int64_t(gridDim.x) - 1) *a.work = 0ull;   // the last ticket of the launch
+        return k;
+    }
     __device__ Tickets(const Args<T>& args, int64_t* s) : a(args), slot(s) {
-        if (threadIdx.x == 0) slot[0] = a.persistent ? int64_t(atomicAdd(a.work, 1ull)) : int64_t(blockIdx.x);
+        if (threadIdx.x == 0) slot[0] = a.persistent ? draw() : int64_t(blockIdx.x);
         __syncthreads();
     }
     __device__ int64_t current() const { const int64_t k = slot[par]; return k < a.nitems ? a.item0 + k : -1; }
     __device__ void prefetch() {
-        if (threadIdx.x == 0) slot[par ^ 1] = a.persistent ? int64_t(atomicAdd(a.work, 1ull)) : a.nitems;
+        if (threadIdx.x == 0) slot[par ^ 1] = a.persistent ? draw() : a.nitems;
     }
     __device__ void advance() { par ^= 1; }
 };
@@ -947,23 +958,49 @@ static inline cudaError_t set_smem_attr(const void* fn, int bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
+// Per device and kernel: the dynamic shared memory granted so far and the
+// occupancy found for it, so that repeated launches make no attribute calls.
+struct LaunchCache {
+    const void* fn;
+    int dev, smem_set, smem_occ, per_sm, nsm;
+};
+
+static cudaError_t launch_shape(const void* fn, int smem, bool persistent, int* resident) {
+    static std::mutex mu;
+    static LaunchCache cache[128];
+    static int ncache = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    LaunchCache* c = nullptr;
+    for (int i = 0; i < ncache; ++i)
+        if (cache[i].fn == fn && cache[i].dev == dev) c = &cache[i];
+    LaunchCache fresh{fn, dev, -1, -1, 0, 0};
+    if (!c) c = ncache < 128 ? &cache[ncache++] : &fresh;
+    if (c->fn != fn || c->dev != dev) *c = fresh;
+    if (smem > c->smem_set) {
+        if ((e = set_smem_attr(fn, smem)) != cudaSuccess) return e;
+        c->smem_set = smem;
+    }
+    if (persistent && smem != c->smem_occ) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        c->smem_occ = smem;
+    }
+    *resident = (c->per_sm > 0 ? c->per_sm : 1) * c->nsm;
+    return cudaSuccess;
+}
+
 // One launch of kernel k: persistent (as many CTAs as can be resident, each
 // drawing work items from the ticket counter) or one CTA per item.
 template <typename T>
 static cudaError_t launch_kernel(void (*k)(Args<T>), const Args<T>& a, int smem, cudaStream_t st) {
-    const void* fn = (const void*)k;
-    cudaError_t e = set_smem_attr(fn, smem);
+    int resident = 0;
+    cudaError_t e = launch_shape((const void*)k, smem, a.persistent != 0, &resident);
     if (e != cudaSuccess) return e;
     unsigned grid = grid_for(a.nitems);
-    if (a.persistent) {
-        int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const int64_t resident = int64_t(per_sm > 0 ? per_sm : 1) * nsm;
-        grid = grid_for(a.nitems < resident ? a.nitems : resident);
-        if ((e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    }
+    if (a.persistent) grid = grid_for(a.nitems < resident ? a.nitems : resident);
     k<<<grid, kThreads, smem, st>>>(a);
     return cudaPeekAtLastError();
 }

@@ -678,6 +678,9 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
         const std::vector<char> tw = twiddle_image(p);
         e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size(), cudaMemcpyHostToDevice);
     }
+    // the persistent launches' ticket counters start at zero (each launch
+    // returns its counter to zero when it ends)
+    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_work, 0, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
     return PSATD_OK;
 }
@@ -876,7 +879,9 @@ int push_into(psatd_plan_s* p, char* base, size_t cap, double c_dt, const double
         for (int a = 0; a < 3; ++a) p->img_dx[a] = dx[a];
         p->img_valid = true;
     }
+    static const unsigned long long zero_work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     struct Part { size_t off; const void* src; size_t n; } parts[] = {
+        {p->off_work, zero_work, sizeof(zero_work)},
         {p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size()},
         {p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size()},
         {p->off_tw, p->img_tw.data(), p->img_tw.size()},
