@@ -113,7 +113,6 @@ __global__ void __launch_bounds__(NT) k_yee(YeeArgs<T> a) {
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * KZ, z1 = min(z0 + KZ, a.nz);
     const int64_t plane = int64_t(a.nx) * a.ny;
-    constexpr bool fast = FAST;
     const unsigned base = smem_addr(smraw);
     const unsigned sE = sizeof(s.e[0]), sB = sizeof(s.bo[0]), sJ = sizeof(s.j[0]);
     const unsigned oE = smem_addr(&s.e[0]) - base, oBo = smem_addr(&s.bo[0]) - base, oJ = smem_addr(&s.j[0]) - base;
@@ -195,14 +194,14 @@ __global__ void __launch_bounds__(NT) k_yee(YeeArgs<T> a) {
         if constexpr (FAST) {
 #pragma unroll
             for (int r = 0; r < KE; ++r) issue(pe[r], slot * sE, zo);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int r = 0; r < PE; ++r) {
-            if (le[r] < 0) continue;
-            const int ey = le[r] / EX, ex = le[r] - (le[r] / EX) * EX;
+            for (int r = 0; r < PE; ++r) {
+                if (le[r] < 0) continue;
+                const int ey = le[r] / EX, ex = le[r] - (le[r] / EX) * EX;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.e[slot][c][ey][ex + V - 1]), a.ein[c] + zo + offE[r]);
+                for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.e[slot][c][ey][ex + V - 1]), a.ein[c] + zo + offE[r]);
+            }
         }
     };
     auto issue_b = [&](int z, int slot) {
@@ -210,14 +209,14 @@ __global__ void __launch_bounds__(NT) k_yee(YeeArgs<T> a) {
         if constexpr (FAST) {
 #pragma unroll
             for (int r = 0; r < KB; ++r) issue(pb[r], slot * sB, zo);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int r = 0; r < PB; ++r) {
-            if (lb[r] < 0) continue;
-            const int by = lb[r] / BX, bx = lb[r] - (lb[r] / BX) * BX;
+            for (int r = 0; r < PB; ++r) {
+                if (lb[r] < 0) continue;
+                const int by = lb[r] / BX, bx = lb[r] - (lb[r] / BX) * BX;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.bo[slot][c][by][bx + V - 1]), a.bin[c] + zo + offB[r]);
+                for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.bo[slot][c][by][bx + V - 1]), a.bin[c] + zo + offB[r]);
+            }
         }
     };
     auto issue_j = [&](int z, int slot) {
@@ -225,11 +224,10 @@ __global__ void __launch_bounds__(NT) k_yee(YeeArgs<T> a) {
         if constexpr (FAST) {
 #pragma unroll
             for (int r = 0; r < KJ; ++r) issue(pj[r], slot * sJ, zo);
-            return;
-        }
-        if (!own) return;
+        } else if (own) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.j[slot][c][ty][tx]), a.jin[c] + zo + offO);
+            for (int c = 0; c < 3; ++c) cp_elem(smem_addr(&s.j[slot][c][ty][tx]), a.jin[c] + zo + offO);
+        }
     };
     // new B at plane z on the tile and its low halo, from E(z) (slot se0),
     // E(z+1) (slot se1) and the old B (slot so) into slot sb; `store`

@@ -110,9 +110,6 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
 
 template <typename T>
 struct cpx4 { T a, b, c, d; };
-template <typename T> struct vec4;
-template <> struct vec4<float> { using type = float4; };
-template <> struct vec4<double> { using type = double4; };
 template <typename T>
 __device__ __forceinline__ void stcs4(T* p, cpx4<T> v) {
     if constexpr (sizeof(T) == 4) {
