@@ -489,7 +489,7 @@ def run_yee(args, rank, world, local_rank):
                    "l2": f"fields ({15 * esz * cells / 1e9:.1f} GB per step) larger than L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
         "roofline": {"bound": "hbm", "kernel": "k_yee", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4), "traffic": _yee_traffic(wl.name), "peak_kind": peak_kind,
                      "alg_bytes_per_cell": 15 * esz},
         "gpu_launches": args.steps * P.psatd_yee_launches(),
         "clocks": clk.summary(),
@@ -616,6 +616,21 @@ def heat_cpu_sample(wl, budget_s: float):
     from oracle import psatd_oracle as O
     return {"value": cells / t_used / 1e9, "unit": "Gcell-steps/s", "cores": O.WORKERS, "kind": "oracle",
             "sample": f"{nsub} of {len(wl.subs)} subdomain steps ({cells} valid cells), {t_used:.1f} s"}
+
+
+def _yee_traffic(workload: str):
+    """DRAM bytes per Yee launch from the committed ncu summary, if it was
+    taken on the current kernel source and this workload's grid (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_yee.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, "paper_1707_08500_gb300", "csrc", "fdtd_yee.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        if t.get("kernel_sha256") != sha or t.get("workload") != workload:
+            return None
+        return t["bytes_per_launch"].get("k_yee")
+    except Exception:
+        return None
 
 
 def yee_cpu_sample(budget_s: float):
