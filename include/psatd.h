@@ -248,6 +248,17 @@ int psatd_geometry_variant(psatd_plan_t plan, int32_t* variant);
 /* Number of kernel launches one psatd_push enqueues for this plan. */
 int psatd_push_launches(psatd_plan_t plan, int32_t* launches);
 
+/* Debug helper: synchronises the device, then returns and clears the plan's
+ * device error word (in its attached workspace; PSATD_E_STATE without one).
+ * Bits: PSATD_CHECK_ITEM -- a work item was decoded outside its subdomain's
+ * item range (the workspace's descriptors were overwritten);
+ * PSATD_CHECK_TICKETS -- a persistent launch drew more tickets than it
+ * issues, i.e. two pushes of the plan overlapped on the GPU (their results
+ * are then undefined).  Kernels set bits and carry on; they never wait. */
+#define PSATD_CHECK_ITEM     0x1
+#define PSATD_CHECK_TICKETS  0x2
+int psatd_check(psatd_plan_t plan, int32_t* error_bits);
+
 #ifdef __cplusplus
 }
 #endif

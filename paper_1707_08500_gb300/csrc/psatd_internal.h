@@ -96,6 +96,7 @@ struct LaunchCommon {
     const void* subs; const void* segs; const void* tw; const void* tab; const void* tabc; void* spec;
     void* eb[6]; const void* jr[4]; double* gauss_part;
     unsigned long long* work;   // persistent-launch work counter (in the workspace)
+    unsigned int* err;          // device error word (bits PSATD_CHECK_*), in the workspace
     int persistent;             // 1: persistent grids drawing tickets; 0: one CTA per work item
     int nsub, nseg, nf, staggered, own_only;
     int nout;             // output fields written by the inverse stages: 6 (E, B) or 1 (heat: T)

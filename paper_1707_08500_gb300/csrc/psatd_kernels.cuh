@@ -84,7 +84,8 @@ struct Args {
     T* eb[6];               // Ex Ey Ez Bx By Bz
     const T* jr[4];         // Jx Jy Jz rho
     double* gauss_part;     // 2 per pass-B item
-    unsigned long long* work;   // work-item ticket counter of this launch (zeroed before it)
+    unsigned long long* work;   // work-item ticket counter of this launch (zero at its start)
+    unsigned int* err;          // device error word: bit 0 item outside its subdomain, bit 1 ticket out of range
     int persistent;         // 1: CTAs draw items from `work`; 0: CTA b does item item0 + b
     int64_t item0, nitems;  // items handled by this launch
     int64_t per_sub[5];     // items per subdomain of each stage when uniform, else 0
@@ -360,6 +361,12 @@ __device__ __forceinline__ int decode_item(const Args<T>& a, int64_t it, SubDesc
             s = find_sub<STAGE>(a.subs, a.nsub, it);
         }
         s = __shfl_sync(0xffffffffu, s, 0);
+        if (threadIdx.x == 0) {
+            // the item must lie in the subdomain's own range of this stage
+            const bool ok = stage_item<STAGE>(a.subs[s]) <= it &&
+                            (s + 1 == a.nsub || it < stage_item<STAGE>(a.subs[s + 1]));
+            if (!ok) atomicOr(a.err, 1u);
+        }
         const int* src = reinterpret_cast<const int*>(a.subs + s);
         int* dst = reinterpret_cast<int*>(sd);
         for (int i = threadIdx.x; i < int(sizeof(SubDesc) / 4); i += 32) dst[i] = __ldg(src + i);
@@ -393,6 +400,10 @@ struct Tickets {
     __device__ int64_t draw() const {
         const int64_t k = int64_t(atomicAdd(a.work, 1ull));
         if (k == a.nitems + int64_t(gridDim.x) - 1) *a.work = 0ull;   // the last ticket of the launch
+        // more tickets than one launch draws: another launch shares the
+        // counter (overlapping pushes of one plan); the ticket is treated as
+        // past the end
+        if (k >= a.nitems + int64_t(gridDim.x)) atomicOr(a.err, 2u);
         return k;
     }
     __device__ Tickets(const Args<T>& args, int64_t* s) : a(args), slot(s) {
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         for (int f = 0; f < nf; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
             cpx<T>* s = sm + f * fs;
-            if (sizeof(T) == 4 && (Q & 1) == 0 && M >= 2) {
+            if (sizeof(T) == 4 && (Q & 1) == 0 && M >= 2 && (M & 1) == 0) {
                 // pairs of modes (16-byte aligned: Q, q0 and M are even),
                 // zero-filled past the ragged end of the plane
                 loop2(M >> 1, Lz, [&](int z, int m2) {
@@ -644,11 +655,21 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_heat(Args<T> a) {
         for (int f = 0; f < nf; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
             cpx<T>* s = sm + f * fs;
-            loop2(M, Lz, [&](int z, int m) {
-                const cpx<T>* gp = src + int64_t(z) * Q + (m < mc ? m : 0);
-                if constexpr (sizeof(T) == 4) cp_async8z(s + z * M + m, gp, m < mc ? 8 : 0);
-                else cp_async16(s + z * M + m, gp, m < mc ? 16 : 0);
-            });
+            if (sizeof(T) == 4 && (Q & 1) == 0 && M >= 2 && (M & 1) == 0) {
+                // pairs of modes, 16-byte copies (Q, q0 and M even), zero-filled
+                // past the ragged end of the plane
+                loop2(M >> 1, Lz, [&](int z, int m2) {
+                    const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<T>));
+                    const cpx<T>* gp = src + int64_t(z) * Q + (nb ? 2 * m2 : 0);
+                    cp_async16(s + z * M + 2 * m2, gp, nb);
+                });
+            } else {
+                loop2(M, Lz, [&](int z, int m) {
+                    const cpx<T>* gp = src + int64_t(z) * Q + (m < mc ? m : 0);
+                    if constexpr (sizeof(T) == 4) cp_async8z(s + z * M + m, gp, m < mc ? 8 : 0);
+                    else cp_async16(s + z * M + m, gp, m < mc ? 16 : 0);
+                });
+            }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -934,6 +955,7 @@ static Args<T> make_args(const LaunchCommon& c, int64_t item0, int64_t nitems) {
     for (int i = 0; i < 4; ++i) a.jr[i] = static_cast<const T*>(c.jr[i]);
     a.gauss_part = c.gauss_part;
     a.work = c.work;
+    a.err = c.err;
     a.persistent = c.persistent;
     a.item0 = item0;
     for (int i = 0; i < 5; ++i) a.per_sub[i] = c.per_sub[i];

@@ -652,6 +652,18 @@ int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
     return PSATD_OK;
 }
 
+int psatd_check(psatd_plan_t p, int32_t* error_bits) {
+    if (!p || !error_bits) return PSATD_E_ARG;
+    if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned int w = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&w, p->ws + p->off_work + 7 * sizeof(unsigned long long), sizeof(w), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_work + 7 * sizeof(unsigned long long), 0, sizeof(w));
+    if (e != cudaSuccess) return cuda_fail(p, e, "read the device error word");
+    *error_bits = int32_t(w);
+    return PSATD_OK;
+}
+
 int psatd_push_launches(psatd_plan_t p, int32_t* n) {
     if (!p || !n) return PSATD_E_ARG;
     int nsub = int(p->desc.size());
@@ -678,8 +690,8 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
         const std::vector<char> tw = twiddle_image(p);
         e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size(), cudaMemcpyHostToDevice);
     }
-    // the persistent launches' ticket counters start at zero (each launch
-    // returns its counter to zero when it ends)
+    // the persistent launches' ticket counters and the error word (the last
+    // slot) start at zero (each launch returns its counter to zero when it ends)
     if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_work, 0, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
     return PSATD_OK;
@@ -742,6 +754,7 @@ static LaunchCommon common_at(psatd_plan_s* p, char* base, const psatd_fields* f
     }
     c.gauss_part = reinterpret_cast<double*>(base + p->off_gauss);
     c.work = reinterpret_cast<unsigned long long*>(base + p->off_work);
+    c.err = reinterpret_cast<unsigned int*>(base + p->off_work + 7 * sizeof(unsigned long long));
     c.persistent = (p->flags & PSATD_GRID_PER_ITEM) ? 0 : 1;
     c.nsub = int(p->desc.size());
     c.nseg = int(p->segs.size());

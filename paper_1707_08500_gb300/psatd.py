@@ -36,7 +36,7 @@ EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_work
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
            "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
-           "psatd_yee_step", "psatd_yee_launches")
+           "psatd_yee_step", "psatd_yee_launches", "psatd_check")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -194,6 +194,13 @@ def psatd_yee_step(global_n: Sequence[int], flags: int, c_dt: float, dx: Sequenc
 def psatd_yee_launches() -> int:
     v = ctypes.c_int32()
     _check(lib().psatd_yee_launches(ctypes.byref(v)))
+    return v.value
+
+
+def psatd_check(plan) -> int:
+    """Synchronise the device and return (and clear) the plan's device error bits."""
+    v = ctypes.c_int32()
+    _check(lib().psatd_check(plan, ctypes.byref(v)), plan)
     return v.value
 
 

@@ -121,6 +121,9 @@ def test_state_errors_without_gpu(P):
         P.psatd_set_coeffs(h, 0.5, (1.0, 1.0, 1.0))
     assert e.value.code == -6
     with pytest.raises(P.PsatdError) as e:
+        P.psatd_check(h)                            # no workspace to read the error word from
+    assert e.value.code == -6
+    with pytest.raises(P.PsatdError) as e:
         P.psatd_set_workspace(h, 0x1001, 1 << 30)   # misaligned: rejected before any copy
     assert e.value.code == -1
     with pytest.raises(P.PsatdError) as e:

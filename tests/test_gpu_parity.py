@@ -147,6 +147,9 @@ def test_repeat_is_deterministic(P):
     b, _ = _run_gpu(P, wl, glob, 3)
     for n in I.EB_NAMES:
         assert torch.equal(a.arenas[n], b.arenas[n])
+    # persistent launches of both runs drew exactly their own tickets, and
+    # every item was decoded inside its subdomain
+    assert P.psatd_check(a.plan) == 0 and P.psatd_check(b.plan) == 0
 
 
 def test_f32_error_over_many_steps(P):
@@ -159,3 +162,21 @@ def test_f32_error_over_many_steps(P):
     err = O.rel_l2(_np(sol.gather_global()), ref)
     print(f"FP32 100-step relative L2 error: {err:.3e}")
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 5, 6])
+def test_pass_b_chunk_widths(P, chunk):
+    """Any chunk width of the z/Eq. 1 stage, odd ones included (element
+    copies instead of 16-byte pairs), against the oracle."""
+    wl = _mixed("f32")
+    glob = I.global_fields(wl)
+    sol = P.Solver(wl, tuning={"chunk_b": chunk, "f1": [0, 0, 0]})
+    sol.load_global(glob, names=I.EB_NAMES, guards=False)
+    sol.load_global(glob, names=("Jx", "Jy", "Jz", "rho"), guards=True)
+    sol.exchange()
+    for _ in range(2):
+        sol.push()
+    torch.cuda.synchronize()
+    ref, _ = _oracle(wl, glob, 2)
+    assert O.rel_l2(_np(sol.gather_global()), ref) < 4e-6
+    assert P.psatd_check(sol.plan) == 0
