@@ -361,18 +361,20 @@ __device__ __forceinline__ int decode_item(const Args<T>& a, int64_t it, SubDesc
             s = find_sub<STAGE>(a.subs, a.nsub, it);
         }
         s = __shfl_sync(0xffffffffu, s, 0);
-        if (threadIdx.x == 0) {
-            // the item must lie in the subdomain's own range of this stage
-            const bool ok = stage_item<STAGE>(a.subs[s]) <= it &&
-                            (s + 1 == a.nsub || it < stage_item<STAGE>(a.subs[s + 1]));
-            if (!ok) atomicOr(a.err, 1u);
-        }
         const int* src = reinterpret_cast<const int*>(a.subs + s);
         int* dst = reinterpret_cast<int*>(sd);
         for (int i = threadIdx.x; i < int(sizeof(SubDesc) / 4); i += 32) dst[i] = __ldg(src + i);
         if (threadIdx.x == 0) s_sub = s;
     }
     __syncthreads();
+    // the item must lie in the subdomain's own range of this stage (checked on
+    // the shared copy: the start, and the count when every subdomain has the
+    // same number of items)
+    if (threadIdx.x == 0) {
+        const int64_t rel = it - stage_item<STAGE>(*sd);
+        const int64_t per = a.per_sub[per_sub_slot<STAGE>()];
+        if (rel < 0 || (per > 0 && rel >= per)) atomicOr(a.err, 1u);
+    }
     return s_sub;
 }
 
