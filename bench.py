@@ -338,7 +338,18 @@ def run_ours(args, rank, world, local_rank):
                 for n in names_in:
                     sets[b][n].copy_(host[n], non_blocking=True)
                 copied[b].record(cs)
+        # warm-up of the copy path (first host-to-device reads of freshly
+        # pinned pages are slower), outside the timed region; then the upload
+        # alone, timed, for reference
+        upload(0)
+        upload(1)
         torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(cs)
+        upload(0)
+        u1.record(cs)
+        torch.cuda.synchronize()
+        upload_ms = u0.elapsed_time(u1)
         e0, e1 = mkev(), mkev()
         e0.record(stream)
         cs.wait_event(e0)
@@ -365,7 +376,7 @@ def run_ours(args, rank, world, local_rank):
         result["e2e"] = {"value": round(replica_value(valid, world, ems), 4), "unit": "Gcell-steps/s",
                          "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
                          "d2h_bytes_per_step": gh[0].numel() * 8 if gauss else 0, "steps": ksteps,
-                         "ms_per_step": round(ems, 3),
+                         "ms_per_step": round(ems, 3), "upload_alone_ms": round(upload_ms, 3),
                          "what": "per step: J (and rho) copied from pinned host (next step's copy overlapping "
                                  "this step's psatd_push, two source sets), psatd_push, Gauss sums read back "
                                  "(on a third stream)"}

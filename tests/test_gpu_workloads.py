@@ -245,3 +245,21 @@ def test_2d_unit_pulse_two_unequal_subdomains(P, precision, tol):
     print(f"2D unit pulse {precision}: GPU vs local oracle {err:.3e}; GPU local vs global {trunc:.3e}")
     assert err < tol
     assert trunc < 2e-4
+
+
+def test_largest_box_f32(P):
+    """The largest supported local box, 512 x 256 x 256 (x half length and the
+    y, z lengths are 16 x 16), as one box over the grid: split-plane schedule,
+    one FP32 step against the oracle."""
+    wl = I.custom("max", (512, 256, 256), ((512,), (256,), (256,)), 0, 32, fields="wavepacket", precision="f32")
+    glob = I.global_fields(wl)
+    sol = _solver(P, wl, glob)
+    assert P.psatd_push_launches(sol.plan) == 5
+    sol.push()
+    torch.cuda.synchronize()
+    ref = dict(_np(glob))
+    ref.update(O.global_push(ref, 32, wl.dx, wl.c_dt, False))
+    err = O.rel_l2(_np(sol.gather_global()), ref)
+    print(f"512x256x256 box, FP32 one step: rel L2 {err:.3e}")
+    assert err < 2e-6
+    assert P.psatd_check(sol.plan) == 0
