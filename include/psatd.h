@@ -13,9 +13,11 @@
  *
  * Memory model: the caller owns ALL device memory (field arenas and one
  * workspace); the library never allocates device memory.  A plan owns only
- * host metadata.  Every call that takes a stream only enqueues work on it: no
- * synchronisation, no allocation, no host read of device data -- so those
- * calls may be captured into a CUDA graph.  A plan is not thread-safe;
+ * host metadata.  psatd_push, psatd_push_profiled, psatd_exchange_guards and
+ * psatd_yee_step only enqueue work on their stream: no synchronisation, no
+ * allocation, no host read of device data -- so they may be captured into a
+ * CUDA graph.  Pushes of one plan must not overlap on the GPU (they share the
+ * plan's workspace; psatd_check reports it).  A plan is not thread-safe;
  * different plans are independent.  psatd_set_workspace and psatd_set_coeffs
  * are set-up calls: they copy metadata and tables to the workspace with
  * blocking copies on the legacy default stream.
@@ -55,7 +57,9 @@ extern "C" {
                                      order-p staggered modified wavenumber and
                                      exact-k phase shifts to nodal position     */
 #define PSATD_GAUSS_DIAG     0x08 /* read rho and return per-subdomain FP64 sums
-                                     of |i[k].E~ - rho~|^2 and |rho~|^2            */
+                                     of |i[k].E~ - rho~|^2 and |rho~|^2 (partial
+                                     sums per work item in the plan's precision,
+                                     accumulated in FP64)                        */
 #define PSATD_PLAIN          0x10 /* baseline schedule: one subdomain per launch,
                                      guards refilled by a separate exchange
                                      kernel (default: all subdomains batched in
