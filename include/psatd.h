@@ -246,7 +246,9 @@ const char* psatd_last_error(psatd_plan_t plan);
 /* Which stage kernels the plan uses: the index of the compiled fixed
  * geometry (every subdomain the same cubic box with default FFT splits:
  * FP32 sides 96/64/48/32 with 16/16/8/0 guards, FP64 96/48/32 with 16/8/0),
- * or -1 for the kernels that read the geometry from each descriptor. */
+ * -2 for the kernels that read the geometry from each descriptor with the
+ * default z/Eq. 1 chunk width (8 modes FP32, 4 FP64) compiled in, or -1 for
+ * the fully descriptor-driven kernels. */
 int psatd_geometry_variant(psatd_plan_t plan, int32_t* variant);
 
 /* Number of kernel launches one psatd_push enqueues for this plan. */

@@ -433,6 +433,19 @@ struct GeoDyn {
           nvy(d.nv[1]), nvz(d.nv[2]), M(d.chunkB), lgM(d.lgB), fs(d.fsB), ax(d.ax), ay(d.ay), az(d.az) {}
 };
 
+// Descriptor-driven geometry with the pass-B chunk width fixed at compile time
+// (the library default), for decompositions of mixed box shapes.
+template <int MB>
+struct GeoDynM {
+    static constexpr bool kFixed = false;
+    static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB);
+    int Lx, Ly, Lz, h, lxh, pitch, q, ng, ngz, nvy, nvz, fs;
+    AxisPlan ax, ay, az;
+    __device__ explicit GeoDynM(const SubDesc& d)
+        : Lx(d.L[0]), Ly(d.L[1]), Lz(d.L[2]), h(d.L[0] >> 1), lxh(d.lxh), pitch(d.pitch), q(d.q), ng(d.ng), ngz(d.ngz),
+          nvy(d.nv[1]), nvz(d.nv[2]), fs(d.fsB), ax(d.ax), ay(d.ay), az(d.az) {}
+};
+
 template <int L, int NG, int MB, int CSZ>
 struct GeoFix {
     static constexpr bool kFixed = true;

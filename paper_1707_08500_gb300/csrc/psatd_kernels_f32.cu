@@ -16,6 +16,7 @@ cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t item0, in
         case 2: return launch_geo<float, GeoF32<2>>(stage, a, smem, st);
         case 3: return launch_geo<float, GeoF32<3>>(stage, a, smem, st);
         case 4: return launch_geo<float, GeoF32<4>>(stage, a, smem, st);
+        case -2: return launch_geo<float, GeoDynM<8>>(stage, a, smem, st);
         default: return launch_geo<float, GeoDyn>(stage, a, smem, st);
     }
 }

@@ -14,6 +14,7 @@ cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t item0, in
         case 0: return launch_geo<double, GeoF64<0>>(stage, a, smem, st);
         case 1: return launch_geo<double, GeoF64<1>>(stage, a, smem, st);
         case 2: return launch_geo<double, GeoF64<2>>(stage, a, smem, st);
+        case -2: return launch_geo<double, GeoDynM<4>>(stage, a, smem, st);
         default: return launch_geo<double, GeoDyn>(stage, a, smem, st);
     }
 }

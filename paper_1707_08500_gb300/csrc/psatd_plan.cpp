@@ -554,6 +554,13 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
             if (ok) p->variant = v;
         }
     }
+    // mixed box shapes with the default chunk width: descriptor-driven
+    // geometry with that width compiled in
+    if (p->variant < 0 && !p->split) {
+        bool dflt = true;
+        for (const SubDesc& d : p->desc) dflt = dflt && d.chunkB == (p->f64 ? 4 : 8);
+        if (dflt) p->variant = -2;
+    }
     if (p->smemB > kPlaneSmemMax || (p->split && std::max(p->smemR, p->smemK) > kPlaneSmemMax))
         return bad(PSATD_E_UNSUPPORTED, "a stage's tile does not fit in shared memory");
     // --- exchange segments (source valid box -> destination local box) ----------

@@ -144,7 +144,7 @@ def test_exchange_segments_cover_every_local_cell_once(P):
 
 def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
     cases = [("mirror1024", P.PSATD_F32, 0), ("broadband256", P.PSATD_F32, 0), ("mirror1024", P.PSATD_F64, 0),
-             ("yee64", P.PSATD_F64 | P.PSATD_STAGGERED, 1), ("plain32", P.PSATD_F64, 2), ("uneven48", P.PSATD_F32, -1)]
+             ("yee64", P.PSATD_F64 | P.PSATD_STAGGERED, 1), ("plain32", P.PSATD_F64, 2), ("uneven48", P.PSATD_F32, -2)]
     for name, flags, want in cases:
         wl = I.workload(name)
         h = P.psatd_plan_create(wl.global_n, wl.subs, flags)
@@ -152,9 +152,14 @@ def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
             assert P.psatd_geometry_variant(h) == want, name
         finally:
             P.psatd_destroy(h)
-    # a non-default split falls back to the descriptor-driven kernels
+    # a non-default split falls back to the descriptor-driven kernels (with
+    # the default chunk width compiled in), a non-default chunk width to the
+    # fully descriptor-driven ones
     wl = I.workload("broadband256")
     h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 8, "f1": [4, 0, 0]})
+    assert P.psatd_geometry_variant(h) == -2
+    P.psatd_destroy(h)
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 6, "f1": [4, 0, 0]})
     assert P.psatd_geometry_variant(h) == -1
     P.psatd_destroy(h)
 

@@ -80,7 +80,7 @@ def test_uneven48_one_step_f32_all_subdomains(P):
     wl = I.workload("uneven48")
     glob = I.global_fields(wl)
     sol = _solver(P, wl, glob, gauss=True)
-    assert P.psatd_geometry_variant(sol.plan) == -1
+    assert P.psatd_geometry_variant(sol.plan) == -2
     sol.push()
     torch.cuda.synchronize()
     gs = []
