@@ -307,21 +307,20 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
     }
     # ---- end to end through the C ABI with per-step host copies ----------------
-    # Every step copies its sources (J, and rho with the Gauss diagnostic)
-    # from pinned host memory and reads the Gauss sums back.  The copies of
-    # step k+1 run on a second stream into a second set of source arenas while
-    # step k computes (double buffering), as a caller streaming sources would.
+    # Every step copies its sources (J, and rho with the Gauss diagnostic) as
+    # global arrays of valid cells from pinned host memory, spreads them into
+    # the padded boxes on the device (psatd_scatter_global: valid cells and
+    # guard images), pushes, and reads the Gauss sums back.  The copy of step
+    # k+1 runs on a second stream into a second device buffer while step k
+    # computes; read-backs use a third stream.
     if not args.skip_e2e:
         names_in = ("Jx", "Jy", "Jz", "rho") if gauss else ("Jx", "Jy", "Jz")
-        host = {n: torch.empty(sol.arena_elems, dtype=sol.dtype, pin_memory=True) for n in names_in}
+        nx, ny, nz = wl.global_n
+        gdev = [{n: torch.empty((nz, ny, nx), dtype=sol.dtype, device=dev) for n in names_in} for _ in range(2)]
+        P.psatd_gather_global(sol.plan, [sol.arenas[n] for n in names_in], [gdev[0][n] for n in names_in], sp)
+        host = {n: torch.empty((nz, ny, nx), dtype=sol.dtype, pin_memory=True) for n in names_in}
         for n in names_in:
-            host[n].copy_(sol.arenas[n])
-        second = {n: torch.empty_like(sol.arenas[n]) for n in names_in}
-        sets = [{n: sol.arenas[n] for n in names_in}, second]
-        fields = [sol.fields, P.make_fields([sol.arenas[n] for n in ("Ex", "Ey", "Ez")],
-                                            [sol.arenas[n] for n in ("Bx", "By", "Bz")],
-                                            [second[n] for n in ("Jx", "Jy", "Jz")],
-                                            second["rho"] if gauss else None)]
+            host[n].copy_(gdev[0][n])
         ksteps = max(3, min(args.steps, 10))
         # one small Gauss buffer per step (device and pinned host), so that no
         # push waits for an earlier step's read-back
@@ -332,19 +331,25 @@ def run_ours(args, rank, world, local_rank):
         pushed = [torch.cuda.Event() for _ in range(ksteps)]   # queue behind the uploads on the copy engines
         copied = [torch.cuda.Event() for _ in range(2)]
         used = [torch.cuda.Event() for _ in range(2)]
+        arenas_in = [sol.arenas[n] for n in names_in]
 
         def upload(b):
             with torch.cuda.stream(cs):
                 for n in names_in:
-                    sets[b][n].copy_(host[n], non_blocking=True)
+                    gdev[b][n].copy_(host[n], non_blocking=True)
                 copied[b].record(cs)
-        # warm-up of the copy path (first host-to-device reads of freshly
-        # pinned pages are slower), outside the timed region; then the upload
-        # alone, timed, for reference
+
+        def step(b, gptr):
+            stream.wait_event(copied[b])
+            P.psatd_scatter_global(sol.plan, [gdev[b][n] for n in names_in], arenas_in, sp)
+            used[b].record(stream)
+            P.psatd_push(sol.plan, sol.fields, gptr, sp)
+        # warm-up of the copy path and of the pushes, outside the timed region;
+        # then the upload alone, timed, for reference
         upload(0)
         upload(1)
-        for b in (0, 1):                 # and of the pushes on both source sets (clocks up)
-            P.psatd_push(sol.plan, fields[b], gd[b].data_ptr() if gauss else None, sp)
+        for b in (0, 1):
+            step(b, gd[b].data_ptr() if gauss else None)
         torch.cuda.synchronize()
         u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         u0.record(cs)
@@ -352,9 +357,12 @@ def run_ours(args, rank, world, local_rank):
         u1.record(cs)
         torch.cuda.synchronize()
         upload_ms = u0.elapsed_time(u1)
-        for b in (0, 1):
-            P.psatd_push(sol.plan, fields[b], gd[b].data_ptr() if gauss else None, sp)
+        s0, s1 = mkev(), mkev()
+        s0.record(stream)
+        P.psatd_scatter_global(sol.plan, [gdev[0][n] for n in names_in], arenas_in, sp)
+        s1.record(stream)
         torch.cuda.synchronize()
+        scatter_ms = s0.elapsed_time(s1)
         e0, e1 = mkev(), mkev()
         e0.record(stream)
         cs.wait_event(e0)
@@ -365,9 +373,7 @@ def run_ours(args, rank, world, local_rank):
                 if k >= 1:
                     cs.wait_event(used[b ^ 1])
                 upload(b ^ 1)
-            stream.wait_event(copied[b])
-            P.psatd_push(sol.plan, fields[b], gd[k].data_ptr() if gauss else None, sp)
-            used[b].record(stream)
+            step(b, gd[k].data_ptr() if gauss else None)
             if gauss:
                 pushed[k].record(stream)
                 ds.wait_event(pushed[k])
@@ -382,10 +388,11 @@ def run_ours(args, rank, world, local_rank):
                          "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
                          "d2h_bytes_per_step": gh[0].numel() * 8 if gauss else 0, "steps": ksteps,
                          "ms_per_step": round(ems, 3), "upload_alone_ms": round(upload_ms, 3),
-                         "what": "per step: J (and rho) copied from pinned host (next step's copy overlapping "
-                                 "this step's psatd_push, two source sets), psatd_push, Gauss sums read back "
-                                 "(on a third stream)"}
-        del host, second, sets, fields
+                         "scatter_ms": round(scatter_ms, 3),
+                         "what": "per step: J (and rho) on the global grid copied from pinned host (the next "
+                                 "step's copy overlapping this step), psatd_scatter_global into the padded "
+                                 "boxes, psatd_push, Gauss sums read back (on a third stream)"}
+        del host, gdev
         torch.cuda.empty_cache()
     # ---- plain FP64 GPU path and FP32-vs-FP64 agreement ------------------------
     if not args.skip_plain and rank == 0:

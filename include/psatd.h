@@ -228,6 +228,22 @@ int psatd_push_profiled(psatd_plan_t plan, const psatd_fields* fields, double* g
 int psatd_push_static(psatd_plan_t plan, double c_dt, const double dx[3], const psatd_fields* fields,
                       double* gauss_dev, void* stream);
 
+/* Global arrays <-> padded-box arenas (the layout of Sec. 3.2 / Fig. 2a).
+ * psatd_scatter_global fills every local cell of every subdomain's box --
+ * valid cells and guard images, read by global index modulo the periodic
+ * grid -- of arenas[f] from global_in[f], for f < nfields (1..10); the result
+ * is what psatd_push expects on entry, so no exchange is needed after it.
+ * psatd_gather_global writes each box's valid cells of arenas[f] into
+ * global_out[f].  Global arrays are dense device arrays [Nz][Ny][Nx] and
+ * arenas are psatd_arena_elems long, both of the plan's precision, owned by
+ * the caller, aligned to the element size; sources and destinations must not
+ * overlap.  Enqueued on `stream`, no allocation; needs the workspace (its copy
+ * descriptors are uploaded by psatd_set_workspace). */
+int psatd_scatter_global(psatd_plan_t plan, const void* const* global_in, void* const* arenas, int32_t nfields,
+                         void* stream);
+int psatd_gather_global(psatd_plan_t plan, const void* const* arenas, void* const* global_out, int32_t nfields,
+                        void* stream);
+
 /* Copy every valid cell into each guard cell that images it (all 26
  * neighbour directions, periodic wrap), for E and B only (T only for
  * PSATD_HEAT plans), on `stream`. */

@@ -15,6 +15,7 @@
 
 #include "psatd.h"
 #include "psatd_internal.h"
+#include "psatd_io.h"
 
 namespace psatd {
 cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
@@ -124,6 +125,9 @@ struct psatd_plan_s {
     std::vector<psatd_sub> subs;
     std::vector<SubDesc> desc;
     std::vector<Segment> segs;
+    std::vector<IoDesc> io;            // global-array <-> arena copy descriptors
+    std::vector<int> io_plane_sub;     // subdomain of every local plane, then of every valid plane
+    int64_t io_planes_local = 0, io_planes_valid = 0;
     int64_t arena_elems = 0;
     int nf = 9;
     bool f64 = false, stag = false, plain = false, diag = false;
@@ -147,6 +151,7 @@ struct psatd_plan_s {
     bool split = false;                // split-plane schedule (row and column launches)
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_work = 0, off_spec = 0, ws_need = 0;
+    size_t off_io = 0, off_io_map = 0;
     int64_t spec_elems = 0;
     char* ws = nullptr;
     size_t ws_size = 0;
@@ -628,6 +633,29 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     p->off_gauss = o; o = align_up(o + size_t(std::max<int64_t>(p->items[1], 1)) * 2 * sizeof(double), 256);
     p->off_work = o; o = align_up(o + 8 * sizeof(unsigned long long), 256);
     p->off_spec = o; o = align_up(o + size_t(p->spec_elems) * 2 * esz, 256);
+    // descriptors of the global-array <-> arena copies
+    for (int s = 0; s < nsub; ++s) {
+        const SubDesc& d = p->desc[s];
+        IoDesc q;
+        std::memset(&q, 0, sizeof(q));
+        q.field_off = d.field_off;
+        q.zstart_local = p->io_planes_local;
+        q.zstart_valid = p->io_planes_valid;
+        for (int a = 0; a < 3; ++a) {
+            q.L[a] = d.L[a];
+            q.g[a] = a == 2 ? d.ngz : d.ng;
+            q.lo[a] = subs[s].lo[a];
+            q.n[a] = subs[s].n[a];
+            q.org[a] = q.lo[a] - q.g[a];
+        }
+        p->io.push_back(q);
+        p->io_planes_local += d.L[2];
+        p->io_planes_valid += d.nv[2];
+    }
+    for (int s = 0; s < nsub; ++s) p->io_plane_sub.insert(p->io_plane_sub.end(), size_t(p->desc[s].L[2]), s);
+    for (int s = 0; s < nsub; ++s) p->io_plane_sub.insert(p->io_plane_sub.end(), size_t(p->desc[s].nv[2]), s);
+    p->off_io = o; o = align_up(o + sizeof(IoDesc) * p->io.size(), 256);
+    p->off_io_map = o; o = align_up(o + sizeof(int) * p->io_plane_sub.size(), 256);
     p->ws_need = o;
     *out = p;
     return PSATD_OK;
@@ -657,6 +685,44 @@ int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
     if (!p || !v) return PSATD_E_ARG;
     *v = p->variant;
     return PSATD_OK;
+}
+
+static int io_call(psatd_plan_s* p, bool scatter, const void* const* src, void* const* dst, int32_t nfields,
+                   void* stream) {
+    if (!p || !src || !dst) return PSATD_E_ARG;
+    if (nfields < 1 || nfields > kIoMaxFields) return fail(p, PSATD_E_ARG, "nfields must be in 1..10");
+    if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
+    IoArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.desc = reinterpret_cast<const IoDesc*>(p->ws + p->off_io);
+    a.plane_sub_local = reinterpret_cast<const int*>(p->ws + p->off_io_map);
+    a.plane_sub_valid = a.plane_sub_local + p->io_planes_local;
+    a.nsub = int(p->desc.size());
+    a.nfields = nfields;
+    for (int i = 0; i < 3; ++i) a.gn[i] = p->gn[i];
+    a.planes_local = p->io_planes_local;
+    a.planes_valid = p->io_planes_valid;
+    const size_t esz = p->f64 ? 8 : 4;
+    for (int f = 0; f < nfields; ++f) {
+        if (!src[f] || !dst[f]) return fail(p, PSATD_E_ARG, "null array");
+        if (reinterpret_cast<uintptr_t>(src[f]) % esz || reinterpret_cast<uintptr_t>(dst[f]) % esz)
+            return fail(p, PSATD_E_ARG, "arrays must be aligned to their element size");
+        a.in[f] = src[f];
+        a.out[f] = dst[f];
+    }
+    cudaError_t e = launch_io(scatter, p->f64, a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(p, e, scatter ? "scatter launch" : "gather launch");
+    return PSATD_OK;
+}
+
+int psatd_scatter_global(psatd_plan_t p, const void* const* global_in, void* const* arenas, int32_t nfields,
+                         void* stream) {
+    return io_call(p, true, global_in, arenas, nfields, stream);
+}
+
+int psatd_gather_global(psatd_plan_t p, const void* const* arenas, void* const* global_out, int32_t nfields,
+                        void* stream) {
+    return io_call(p, false, arenas, global_out, nfields, stream);
 }
 
 int psatd_check(psatd_plan_t p, int32_t* error_bits) {
@@ -693,6 +759,11 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
         e = cudaMemcpy(p->ws + p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy segments"); }
     }
+    e = cudaMemcpy(p->ws + p->off_io, p->io.data(), sizeof(IoDesc) * p->io.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->ws + p->off_io_map, p->io_plane_sub.data(), sizeof(int) * p->io_plane_sub.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy the copy descriptors"); }
     {
         const std::vector<char> tw = twiddle_image(p);
         e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size(), cudaMemcpyHostToDevice);

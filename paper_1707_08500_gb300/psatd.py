@@ -36,7 +36,8 @@ EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_work
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
            "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
-           "psatd_yee_step", "psatd_yee_launches", "psatd_check")
+           "psatd_yee_step", "psatd_yee_launches", "psatd_check", "psatd_scatter_global",
+           "psatd_gather_global")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -195,6 +196,25 @@ def psatd_yee_launches() -> int:
     v = ctypes.c_int32()
     _check(lib().psatd_yee_launches(ctypes.byref(v)))
     return v.value
+
+
+def _ptrs(ts) -> "ctypes.Array":
+    return (ctypes.c_void_p * len(ts))(*[t if isinstance(t, int) else t.data_ptr() for t in ts])
+
+
+def psatd_scatter_global(plan, global_in: Sequence, arenas: Sequence, stream: Optional[int] = None):
+    """Fill every padded box (valid cells and guards) of each arena from a
+    global [Nz][Ny][Nx] device array (tensors or raw pointers)."""
+    assert len(global_in) == len(arenas)
+    _check(lib().psatd_scatter_global(plan, _ptrs(global_in), _ptrs(arenas), ctypes.c_int32(len(arenas)),
+                                      ctypes.c_void_p(stream or 0)), plan)
+
+
+def psatd_gather_global(plan, arenas: Sequence, global_out: Sequence, stream: Optional[int] = None):
+    """Write each box's valid cells of each arena into a global device array."""
+    assert len(global_out) == len(arenas)
+    _check(lib().psatd_gather_global(plan, _ptrs(arenas), _ptrs(global_out), ctypes.c_int32(len(arenas)),
+                                     ctypes.c_void_p(stream or 0)), plan)
 
 
 def psatd_check(plan) -> int:

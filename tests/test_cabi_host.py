@@ -267,3 +267,17 @@ def test_heat_plans(P):
         with pytest.raises(P.PsatdError) as e:
             P.psatd_plan_create(g, subs, flags)
         assert e.value.code == -1
+
+
+def test_scatter_gather_argument_checks(P):
+    wl = I.workload("plain32")
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F64)
+    try:
+        with pytest.raises(P.PsatdError) as e:
+            P.psatd_scatter_global(h, [0x1000], [0x2000])     # no workspace yet
+        assert e.value.code == -6
+        with pytest.raises(P.PsatdError) as e:
+            P.psatd_gather_global(h, [0x1000] * 11, [0x2000] * 11)
+        assert e.value.code == -1
+    finally:
+        P.psatd_destroy(h)
