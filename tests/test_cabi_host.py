@@ -69,7 +69,8 @@ def test_plain_schedule_launch_count(P):
 @pytest.mark.parametrize("case,code", [
     ("overlap", -2), ("gap", -2), ("outside", -2), ("odd_order", -2),
     ("odd_local_x", -5), ("big_prime", -5), ("no_precision", -1), ("both_precisions", -1), ("no_subdomains", -1),
-    ("unknown_flag", -1), ("negative_guard", -2),
+    ("unknown_flag", -1), ("negative_guard", -2), ("empty_global", -2), ("empty_subdomain", -2),
+    ("negative_global", -2), ("two_d_with_z", -2),
 ])
 def test_plan_rejects_bad_input(P, case, code):
     g = (32, 32, 32)
@@ -99,6 +100,14 @@ def test_plan_rejects_bad_input(P, case, code):
         flags = P.PSATD_F32 | 0x400
     elif case == "negative_guard":
         subs = [I.Sub(s.lo, s.n, -1, 8) for s in subs]
+    elif case == "empty_global":
+        g = (0, 32, 32)
+    elif case == "empty_subdomain":
+        subs = [I.Sub((0, 0, 0), (32, 32, 0), 0, 8)]
+    elif case == "negative_global":
+        g = (-4, 32, 32)
+    elif case == "two_d_with_z":
+        flags |= P.PSATD_2D
     with pytest.raises(P.PsatdError) as e:
         P.psatd_plan_create(g, subs, flags)
     assert e.value.code == code
