@@ -51,3 +51,17 @@ def test_two_gloo_ranks_take_the_slowest_time():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.replica_value(268435456, 1, 100.0) == pytest.approx(2.68435456)
+
+
+def test_stage_byte_model_matches_the_documented_per_cell_figures():
+    """Algorithmic bytes per local cell of the three stages on 96^3 boxes with
+    16 guards, FP32, 10 fields in (80.8, 57.2 and 40.3 B per local cell)."""
+    import bench
+    from paper_1707_08500_gb300 import inputs as I
+    wl = I.workload("mirror1024")
+    by, local = bench.stage_bytes(wl, 10, 4)
+    per = {k: v / local for k, v in by.items()}
+    assert abs(per["A"] - 80.83) < 0.01 and abs(per["B"] - 57.17) < 0.01 and abs(per["C"] - 40.33) < 0.01, per
+    # heat: two fields in, one out
+    by, _ = bench.stage_bytes(wl, 2, 4, nout=1)
+    assert abs(by["A"] / local - 2 * (4 + 49 * 8 / 96)) < 1e-6
