@@ -16,6 +16,13 @@ namespace {
 
 constexpr int kIoThreads = 256;
 
+// 16-byte vector of T
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 __device__ __forceinline__ int wrap(int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;
@@ -34,6 +41,20 @@ __global__ void __launch_bounds__(kIoThreads) k_scatter(IoArgs a) {
     const T* __restrict__ in = static_cast<const T*>(a.in[f]) + int64_t(gz) * a.gn[1] * a.gn[0];
     T* __restrict__ out = static_cast<T*>(a.out[f]) + d.field_off + int64_t(z) * Ly * Lx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // rows that do not wrap and start on 16-byte boundaries on both sides move
+    // as 16-byte vectors
+    constexpr int V = 16 / int(sizeof(T));
+    using V16 = typename Vec16<T>::type;
+    if (d.org[0] >= 0 && d.org[0] + Lx <= a.gn[0] && d.org[0] % V == 0 && a.gn[0] % V == 0 && Lx % V == 0 &&
+        aligned16(in) && aligned16(out)) {
+        const int nv = Lx / V;
+        for (int y = warp; y < Ly; y += kIoThreads / 32) {
+            const V16* row = reinterpret_cast<const V16*>(in + int64_t(wrap(d.org[1] + y, a.gn[1])) * a.gn[0] + d.org[0]);
+            V16* orow = reinterpret_cast<V16*>(out + int64_t(y) * Lx);
+            for (int x = lane; x < nv; x += 32) orow[x] = __ldg(row + x);
+        }
+        return;
+    }
     const int gx0 = wrap(d.org[0] + lane, a.gn[0]);
     for (int y = warp; y < Ly; y += kIoThreads / 32) {
         const T* row = in + int64_t(wrap(d.org[1] + y, a.gn[1])) * a.gn[0];
@@ -61,6 +82,17 @@ __global__ void __launch_bounds__(kIoThreads) k_gather(IoArgs a) {
     T* __restrict__ out = static_cast<T*>(a.out[f]) +
                           (int64_t(d.lo[2] + zv) * a.gn[1] + d.lo[1]) * a.gn[0] + d.lo[0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int V = 16 / int(sizeof(T));
+    using V16 = typename Vec16<T>::type;
+    if (d.n[0] % V == 0 && Lx % V == 0 && a.gn[0] % V == 0 && aligned16(in) && aligned16(out)) {
+        const int nv = d.n[0] / V;
+        for (int y = warp; y < d.n[1]; y += kIoThreads / 32) {
+            const V16* row = reinterpret_cast<const V16*>(in + int64_t(y) * Lx);
+            V16* orow = reinterpret_cast<V16*>(out + int64_t(y) * a.gn[0]);
+            for (int x = lane; x < nv; x += 32) orow[x] = __ldg(row + x);
+        }
+        return;
+    }
     for (int y = warp; y < d.n[1]; y += kIoThreads / 32) {
         const T* row = in + int64_t(y) * Lx;
         T* orow = out + int64_t(y) * a.gn[0];
