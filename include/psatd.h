@@ -244,6 +244,15 @@ int psatd_scatter_global(psatd_plan_t plan, const void* const* global_in, void* 
 int psatd_gather_global(psatd_plan_t plan, const void* const* arenas, void* const* global_out, int32_t nfields,
                         void* stream);
 
+/* Introspection of the guard exchange (Fig. 3 step 3) the plan built (host
+ * only).  *count receives the number of copy segments; if segs is not NULL it
+ * receives 12 int32 per segment: source subdomain, destination subdomain,
+ * first source local cell (x, y, z), extents (x, y, z), offset from source
+ * local to destination local coordinates (x, y, z), and 1 for a subdomain's
+ * own valid box (0 for a guard image).  Every local cell of every box is the
+ * destination of exactly one segment cell. */
+int psatd_exchange_segments(psatd_plan_t plan, int32_t* count, int32_t* segs);
+
 /* Copy every valid cell into each guard cell that images it (all 26
  * neighbour directions, periodic wrap), for E and B only (T only for
  * PSATD_HEAT plans), on `stream`. */

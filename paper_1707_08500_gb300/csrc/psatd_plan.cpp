@@ -725,6 +725,19 @@ int psatd_gather_global(psatd_plan_t p, const void* const* arenas, void* const* 
     return io_call(p, false, arenas, global_out, nfields, stream);
 }
 
+int psatd_exchange_segments(psatd_plan_t p, int32_t* count, int32_t* segs) {
+    if (!p || !count) return PSATD_E_ARG;
+    *count = int32_t(p->segs.size());
+    if (segs) {
+        for (size_t i = 0; i < p->segs.size(); ++i) {
+            const Segment& g = p->segs[i];
+            const int32_t v[12] = {g.src, g.dst, g.x0, g.y0, g.z0, g.ex, g.ey, g.ez, g.dx, g.dy, g.dz, g.identity};
+            std::memcpy(segs + 12 * i, v, sizeof(v));
+        }
+    }
+    return PSATD_OK;
+}
+
 int psatd_check(psatd_plan_t p, int32_t* error_bits) {
     if (!p || !error_bits) return PSATD_E_ARG;
     if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");

@@ -37,7 +37,7 @@ EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_work
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
            "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
            "psatd_yee_step", "psatd_yee_launches", "psatd_check", "psatd_scatter_global",
-           "psatd_gather_global")
+           "psatd_gather_global", "psatd_exchange_segments")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -215,6 +215,16 @@ def psatd_gather_global(plan, arenas: Sequence, global_out: Sequence, stream: Op
     assert len(global_out) == len(arenas)
     _check(lib().psatd_gather_global(plan, _ptrs(arenas), _ptrs(global_out), ctypes.c_int32(len(arenas)),
                                      ctypes.c_void_p(stream or 0)), plan)
+
+
+def psatd_exchange_segments(plan):
+    """The plan's guard-exchange copy segments as a list of 12-int tuples
+    (src, dst, x0, y0, z0, ex, ey, ez, dx, dy, dz, identity)."""
+    n = ctypes.c_int32()
+    _check(lib().psatd_exchange_segments(plan, ctypes.byref(n), None), plan)
+    buf = (ctypes.c_int32 * (12 * n.value))()
+    _check(lib().psatd_exchange_segments(plan, ctypes.byref(n), buf), plan)
+    return [tuple(buf[12 * i:12 * i + 12]) for i in range(n.value)]
 
 
 def psatd_check(plan) -> int:

@@ -290,3 +290,54 @@ def test_scatter_gather_argument_checks(P):
         assert e.value.code == -1
     finally:
         P.psatd_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["mixed", "wide_guard", "two_d", "uneven48", "one_box", "thin"])
+def test_exchange_segments_write_every_local_cell_once_from_its_owner(P, name):
+    """Host check of the plan's guard exchange (Fig. 3 step 3): every local
+    cell of every padded box is the destination of exactly one segment cell,
+    whose source is a valid cell of the subdomain that owns the same global
+    cell (global index modulo the periodic grid)."""
+    import numpy as np
+    from oracle import psatd_oracle as O
+    two_d = False
+    if name == "mixed":
+        g, subs = (32, 27, 35), I.tensor_decomposition((12, 20), (14, 13), (18, 17), 4, 8)
+    elif name == "wide_guard":
+        g, subs = (40, 16, 16), I.tensor_decomposition([8, 32], [16], [16], 10, 6)
+    elif name == "two_d":
+        wl = I.custom("t2", (48, 30, 1), ((30, 18), (16, 14), (1,)), 6, 16, two_d=True)
+        g, subs, two_d = wl.global_n, wl.subs, True
+    elif name == "uneven48":
+        wl = I.workload("uneven48")
+        g, subs = wl.global_n, wl.subs
+    elif name == "one_box":
+        g, subs = (16, 12, 8), [I.Sub((0, 0, 0), (16, 12, 8), 3, 8)]
+    else:
+        g, subs = (20, 12, 12), I.tensor_decomposition([2, 18], [12], [12], 3, 6)
+    h = P.psatd_plan_create(g, subs, P.PSATD_F32 | (P.PSATD_2D if two_d else 0))
+    try:
+        segs = P.psatd_exchange_segments(h)
+    finally:
+        P.psatd_destroy(h)
+    owner = O.owner_map(g, subs)                     # [Nz][Ny][Nx] -> owning subdomain
+    guards = [O.sub_guards(sd) for sd in subs]
+    cover = [np.zeros(sd.local[::-1], dtype=np.int32) for sd in subs]
+    for (src, dst, x0, y0, z0, ex, ey, ez, dx, dy, dz, ident) in segs:
+        s, d = subs[src], subs[dst]
+        gs, gd = guards[src], guards[dst]
+        # source cells are valid cells of the source subdomain
+        assert gs[0] <= x0 and x0 + ex <= gs[0] + s.n[0]
+        assert gs[1] <= y0 and y0 + ey <= gs[1] + s.n[1]
+        assert gs[2] <= z0 and z0 + ez <= gs[2] + s.n[2]
+        assert not ident or (src == dst and (dx, dy, dz) == (0, 0, 0))
+        zz, yy, xx = np.meshgrid(np.arange(z0, z0 + ez), np.arange(y0, y0 + ey), np.arange(x0, x0 + ex), indexing="ij")
+        # the destination cell images the same global cell, which the source owns
+        gsx, gsy, gsz = (s.lo[0] - gs[0] + xx) % g[0], (s.lo[1] - gs[1] + yy) % g[1], (s.lo[2] - gs[2] + zz) % g[2]
+        tx, ty, tz = xx + dx, yy + dy, zz + dz
+        gdx, gdy, gdz = (d.lo[0] - gd[0] + tx) % g[0], (d.lo[1] - gd[1] + ty) % g[1], (d.lo[2] - gd[2] + tz) % g[2]
+        assert np.array_equal(gsx, gdx) and np.array_equal(gsy, gdy) and np.array_equal(gsz, gdz)
+        assert (owner[gsz, gsy, gsx] == src).all()
+        np.add.at(cover[dst], (tz, ty, tx), 1)
+    for c in cover:
+        assert (c == 1).all()
