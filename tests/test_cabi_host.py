@@ -292,7 +292,7 @@ def test_scatter_gather_argument_checks(P):
         P.psatd_destroy(h)
 
 
-@pytest.mark.parametrize("name", ["mixed", "wide_guard", "two_d", "uneven48", "one_box", "thin"])
+@pytest.mark.parametrize("name", ["mixed", "wide_guard", "two_d", "uneven48", "one_box", "thin", "guard_wider_than_grid"])
 def test_exchange_segments_write_every_local_cell_once_from_its_owner(P, name):
     """Host check of the plan's guard exchange (Fig. 3 step 3): every local
     cell of every padded box is the destination of exactly one segment cell,
@@ -313,8 +313,10 @@ def test_exchange_segments_write_every_local_cell_once_from_its_owner(P, name):
         g, subs = wl.global_n, wl.subs
     elif name == "one_box":
         g, subs = (16, 12, 8), [I.Sub((0, 0, 0), (16, 12, 8), 3, 8)]
-    else:
+    elif name == "thin":
         g, subs = (20, 12, 12), I.tensor_decomposition([2, 18], [12], [12], 3, 6)
+    else:                        # guards wrap around the periodic grid more than once
+        g, subs = (8, 6, 4), I.tensor_decomposition([4, 4], [6], [4], 10, 4)
     h = P.psatd_plan_create(g, subs, P.PSATD_F32 | (P.PSATD_2D if two_d else 0))
     try:
         segs = P.psatd_exchange_segments(h)
