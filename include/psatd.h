@@ -244,6 +244,16 @@ int psatd_scatter_global(psatd_plan_t plan, const void* const* global_in, void* 
 int psatd_gather_global(psatd_plan_t plan, const void* const* arenas, void* const* global_out, int32_t nfields,
                         void* stream);
 
+/* Introspection of the coefficient tables (host only, no CUDA call): the
+ * real table image psatd_set_coeffs would upload for (c_dt, dx), in the
+ * plan's precision.  For one table set (the subdomains sharing a local shape,
+ * order and FFT factorisation, in order of first use), 7 arrays of
+ * Lz*Ly*(Lx/2+1) values -- C, S, S/k, 1-C, (1-C)/k, S/k - dt (all scaled by
+ * 1/(Lx Ly Lz)) and 1/k -- in the position order of the forward transforms,
+ * padded to 64 elements, then [k] of the x (Lx/2+1), y and z positions, padded
+ * to 64.  out == NULL: *bytes receives the size. */
+int psatd_debug_tables(psatd_plan_t plan, double c_dt, const double dx[3], void* out, size_t* bytes);
+
 /* Introspection of the guard exchange (Fig. 3 step 3) the plan built (host
  * only).  *count receives the number of copy segments; if segs is not NULL it
  * receives 12 int32 per segment: source subdomain, destination subdomain,

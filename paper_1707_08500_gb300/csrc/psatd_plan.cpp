@@ -725,6 +725,19 @@ int psatd_gather_global(psatd_plan_t p, const void* const* arenas, void* const* 
     return io_call(p, false, arenas, global_out, nfields, stream);
 }
 
+int psatd_debug_tables(psatd_plan_t p, double c_dt, const double dx[3], void* out, size_t* bytes) {
+    if (!p || !bytes || !dx) return PSATD_E_ARG;
+    if (!(c_dt == c_dt) || !(dx[0] > 0 && dx[1] > 0 && dx[2] > 0)) return fail(p, PSATD_E_ARG, "bad c_dt or dx");
+    std::vector<char> tab, tabc;
+    table_images(p, c_dt, dx, tab, tabc);
+    if (out) {
+        if (*bytes < tab.size()) return fail(p, PSATD_E_NOMEM, "buffer smaller than the table image");
+        std::memcpy(out, tab.data(), tab.size());
+    }
+    *bytes = tab.size();
+    return PSATD_OK;
+}
+
 int psatd_exchange_segments(psatd_plan_t p, int32_t* count, int32_t* segs) {
     if (!p || !count) return PSATD_E_ARG;
     *count = int32_t(p->segs.size());

@@ -37,7 +37,7 @@ EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_work
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
            "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
            "psatd_yee_step", "psatd_yee_launches", "psatd_check", "psatd_scatter_global",
-           "psatd_gather_global", "psatd_exchange_segments")
+           "psatd_gather_global", "psatd_exchange_segments", "psatd_debug_tables")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -215,6 +215,16 @@ def psatd_gather_global(plan, arenas: Sequence, global_out: Sequence, stream: Op
     assert len(global_out) == len(arenas)
     _check(lib().psatd_gather_global(plan, _ptrs(arenas), _ptrs(global_out), ctypes.c_int32(len(arenas)),
                                      ctypes.c_void_p(stream or 0)), plan)
+
+
+def psatd_debug_tables(plan, c_dt: float, dx: Sequence[float]) -> bytes:
+    """The real coefficient-table image the plan would upload (host only)."""
+    d = (ctypes.c_double * 3)(*dx)
+    n = ctypes.c_size_t(0)
+    _check(lib().psatd_debug_tables(plan, ctypes.c_double(c_dt), d, None, ctypes.byref(n)), plan)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().psatd_debug_tables(plan, ctypes.c_double(c_dt), d, buf, ctypes.byref(n)), plan)
+    return buf.raw
 
 
 def psatd_exchange_segments(plan):

@@ -343,3 +343,48 @@ def test_exchange_segments_write_every_local_cell_once_from_its_owner(P, name):
         np.add.at(cover[dst], (tz, ty, tx), 1)
     for c in cover:
         assert (c == 1).all()
+
+
+@pytest.mark.parametrize("p_order,staggered", [(8, False), (4, True), (0, False)])
+def test_coefficient_tables_match_the_oracle(P, p_order, staggered):
+    """Host check of the Eq. 1 tables the plan builds (Sec. 3.1): the FP64
+    image for one 12 x 10 x 8 box with explicit FFT splits, read back in the
+    forward transforms' position order and mapped to natural indices, against
+    the oracle's modified wavenumbers and Eq. 1 coefficients."""
+    import numpy as np
+    from oracle import psatd_oracle as O
+    L, f1 = (12, 10, 8), (2, 5, 4)
+    dx, c_dt = (1.0, 0.8, 1.25), 0.45
+    flags = P.PSATD_F64 | (P.PSATD_STAGGERED if staggered else 0)
+    h = P.psatd_plan_create(L, [I.Sub((0, 0, 0), L, 0, p_order)], flags, {"chunk_b": 0, "f1": list(f1)})
+    try:
+        img = np.frombuffer(P.psatd_debug_tables(h, c_dt, dx), dtype=np.float64)
+    finally:
+        P.psatd_destroy(h)
+    hx = L[0] // 2
+    lxh = hx + 1
+    n = (hx, L[1], L[2])
+
+    def nat(a, P_):
+        f2 = n[a] // f1[a]
+        return hx if (a == 0 and P_ == hx) else P_ // f2 + f1[a] * (P_ % f2)
+    natx = np.array([nat(0, q) for q in range(lxh)])
+    naty = np.array([nat(1, q) for q in range(L[1])])
+    natz = np.array([nat(2, q) for q in range(L[2])])
+    km = [O.modified_k(L[a], dx[a], p_order, staggered) for a in range(3)]
+    kx, ky, kz = km[0][natx], km[1][naty], km[2][natz]
+    NM = L[2] * L[1] * lxh
+    koff = (7 * NM + 63) // 64 * 64
+    assert np.allclose(img[koff:koff + lxh], kx, rtol=1e-14, atol=1e-14)
+    assert np.allclose(img[koff + lxh:koff + lxh + L[1]], ky, rtol=1e-14, atol=1e-14)
+    assert np.allclose(img[koff + lxh + L[1]:koff + lxh + L[1] + L[2]], kz, rtol=1e-14, atol=1e-14)
+    KX, KY, KZ = np.meshgrid(kx, ky, kz, indexing="ij")
+    kmag = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2).transpose(2, 1, 0)      # [z][y][x] positions
+    co = O.eq1_coefficients(kmag, c_dt)
+    inv = np.where(kmag > 0, 1.0 / np.where(kmag > 0, kmag, 1.0), 0.0)
+    invN = 1.0 / (L[0] * L[1] * L[2])
+    want = [co["C"] * invN, co["S"] * invN, co["S_k"] * invN, co["omC"] * invN, co["omC_k"] * invN,
+            co["Sk_dt"] * invN, inv]
+    for t, w in enumerate(want):
+        got = img[t * NM:(t + 1) * NM].reshape(L[2], L[1], lxh)
+        np.testing.assert_allclose(got, w, rtol=1e-12, atol=1e-15 * (1.0 if t < 6 else 10.0), err_msg=str(t))
