@@ -65,3 +65,24 @@ def test_stage_byte_model_matches_the_documented_per_cell_figures():
     # heat: two fields in, one out
     by, _ = bench.stage_bytes(wl, 2, 4, nout=1)
     assert abs(by["A"] / local - 2 * (4 + 49 * 8 / 96)) < 1e-6
+
+
+@pytest.mark.parametrize("solver", ["psatd", "yee", "heat"])
+def test_reference_arm_prints_one_json_line(solver):
+    """bench.py --impl reference runs the FP64 oracle on the host cores and
+    prints one JSON line with the reference fields (no GPU involved)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    args = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3",
+            "--ref-subs", "1", "--cpu-budget", "1", "--solver", solver]
+    if solver == "heat":
+        args += ["--workload", "plain32"]
+    r = subprocess.run(args, capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
