@@ -40,7 +40,9 @@ design notes of the repository):
 Parity pins: FD weights against exact rational moment solutions; the FFT
 wrapper against a brute-force DFT; the per-mode update against the matrix
 exponential of the Maxwell ODE with constant J; real-space plane waves against
-the closed-form solution (dispersion); energy and Gauss invariants; local
+the closed-form solution (dispersion); energy and Gauss invariants; the two
+Gauss-diagnostic sums against N times real-space sums of (div_p E' - rho)^2 and
+rho^2 (an order-p stencil evaluated without transforms, and Parseval); local
 equals global when the padded box is one global period; guard-truncation error
 decreasing with the guard count.  The magnitude of the guard-truncation error
 is parity unpinned (its model is in another paper).

@@ -125,3 +125,49 @@ def test_nyquist_mode_decays():
     T = (-1.0) ** x
     out = H.heat_global_push(T, None, 2, DX, 0.05)
     np.testing.assert_allclose(out, math.exp(-0.05 * sum(4 / d ** 2 for d in DX)) * T, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each plausible error in the oracle fails a pin above
+# --------------------------------------------------------------------------
+def _pin_errors():
+    """Largest deviation of each closed-form pin above, in one dict."""
+    out = {}
+    m = (3, -2, 5)
+    k = [2 * math.pi * m[a] / (N[a] * DX[a]) for a in range(3)]
+    x, y, z = _grid(N, DX)
+    T = np.cos(k[0] * x + k[1] * y + k[2] * z)
+    kk = [2 * math.sin(k[a] * DX[a] / 2) / DX[a] for a in range(3)]
+    xx = 0.7 * sum(v * v for v in kk)
+    out["mode"] = float(np.abs(H.heat_global_push(T, None, 2, DX, 0.7) - math.exp(-xx) * T).max())
+    out["source"] = float(np.abs(H.heat_global_push(np.zeros_like(T), T, 2, DX, 0.7) + math.expm1(-xx) / xx * T).max())
+    chk = (-1.0) ** np.indices(T.shape).sum(axis=0)
+    out["nyquist"] = float(np.abs(H.heat_global_push(chk, None, 2, DX, 0.05) -
+                                  math.exp(-0.05 * sum(4 / d ** 2 for d in DX)) * chk).max())
+    return out
+
+
+def _mutant(name):
+    k2, fac = H.heat_k2, H.heat_factors
+    if name == "ignored_cell_size":
+        return "heat_k2", lambda L, du, p: k2(L, 1.0, p)
+    if name == "doubled_dt":
+        return "heat_factors", lambda kk, d_dt: fac(kk, 2 * d_dt)
+    if name == "dropped_source_factor":
+        return "heat_factors", lambda kk, d_dt: (fac(kk, d_dt)[0], np.ones_like(kk))
+    if name == "nodal_weights":
+        from oracle import psatd_oracle as O
+
+        def nodal(L, du, p):
+            km = O.modified_k(L, du, p, False)
+            return km * km
+        return "heat_k2", nodal
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name", ["ignored_cell_size", "doubled_dt", "dropped_source_factor", "nodal_weights"])
+def test_pins_catch_planted_mistakes(monkeypatch, name):
+    assert max(_pin_errors().values()) < 1e-12
+    attr, fn = _mutant(name)
+    monkeypatch.setattr(H, attr, fn)
+    assert max(_pin_errors().values()) > 1e-3

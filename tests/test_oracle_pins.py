@@ -292,6 +292,89 @@ def test_gauss_law_preserved_with_continuity(p, staggered):
 
 
 # --------------------------------------------------------------------------
+# the Gauss diagnostic's two sums, pinned against real-space evaluations
+# --------------------------------------------------------------------------
+def _real_space_div(f, dx, p, staggered):
+    """Order-p divergence of (Ex, Ey, Ez) at the nodes of a periodic box,
+    evaluated as a real-space stencil (no transform): nodal
+    sum_j w_j (F[i+j] - F[i-j]) / du; staggered (component u stored at index i
+    stands for position i + 1/2 along u) sum_j c_j (F[i+j-1] - F[i-j]) / du.
+    Weights are the exact rational solutions of the moment conditions."""
+    w = [float(v) for v in exact_weights(p, staggered)]
+    div = 0.0
+    for comp, axis, du in (("Ex", 2, dx[0]), ("Ey", 1, dx[1]), ("Ez", 0, dx[2])):
+        F = f[comp]
+        for j, wj in enumerate(w, start=1):
+            if staggered:
+                div = div + wj * (np.roll(F, -(j - 1), axis) - np.roll(F, j, axis)) / du
+            else:
+                div = div + wj * (np.roll(F, -j, axis) - np.roll(F, j, axis)) / du
+    return div
+
+
+def _gauss_pin_case(shape, p, staggered, seed=3):
+    """One oracle step of a single periodic box (no guards) on random,
+    non-conserving fields; returns the oracle's two sums and their real-space
+    values: N * sum (div_p E' - rho)^2 and N * sum rho^2 (Parseval, N cells)."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    wl = I.custom("g", shape, ((nx,), (ny,), (nz,)), 0, p, staggered=staggered, c_dt=0.55)
+    wl = dataclasses.replace(wl, dx=(0.9, 1.3, 0.7))
+    f = {nm: rng.standard_normal((nz, ny, nx)) for nm in O.EB + ("Jx", "Jy", "Jz", "rho")}
+    gs = []
+    g = O.step(f, wl, gauss_out=gs)
+    N = nx * ny * nz
+    res2_rs = N * float(np.sum((_real_space_div(g, wl.dx, p, staggered) - f["rho"]) ** 2))
+    rho2_rs = N * float(np.sum(f["rho"] ** 2))
+    return gs[0], (res2_rs, rho2_rs)
+
+
+@pytest.mark.parametrize("shape,p,staggered", [((9, 7, 5), 4, False), ((10, 6, 8), 8, False),
+                                               ((12, 5, 7), 2, False), ((9, 7, 11), 4, True),
+                                               ((11, 9, 5), 6, True)])
+def test_gauss_sums_equal_real_space_residual(shape, p, staggered):
+    """res2 = sum over the full spectrum of |i[k].E~' - rho~|^2 equals N times
+    the real-space sum of (div_p E' - rho)^2, and rho2 equals N sum rho^2
+    (Parseval).  Even x lengths exercise the Nyquist column's multiplicity;
+    odd ones the absent Nyquist column.  Staggered cases use odd lengths (the
+    Nyquist reading makes the staggered [k] differ from the stencil there)."""
+    (res2, rho2), (res2_rs, rho2_rs) = _gauss_pin_case(shape, p, staggered)
+    assert res2_rs > 1.0 and rho2_rs > 1.0
+    assert abs(res2 - res2_rs) <= 1e-11 * res2_rs, (res2, res2_rs)
+    assert abs(rho2 - rho2_rs) <= 1e-12 * rho2_rs, (rho2, rho2_rs)
+
+
+@pytest.mark.parametrize("shape,mutant", [((10, 6, 8), "all_two"), ((10, 6, 8), "first_two"),
+                                          ((10, 6, 8), "nyquist_two"), ((9, 7, 5), "all_two"),
+                                          ((9, 7, 5), "first_two"), ((9, 7, 5), "last_one")])
+def test_gauss_pin_catches_wrong_multiplicity(monkeypatch, shape, mutant):
+    """A planted mistake in the half-spectrum multiplicities of the oracle
+    (every column counted twice; the kx = 0 column counted twice; the Nyquist
+    column of an even axis counted twice; the last column of an odd axis
+    counted once) makes the pin above fail."""
+    good = O.half_weights
+
+    def bad(Lx):
+        w = good(Lx).copy()
+        if mutant == "all_two":
+            w[:] = 2.0
+        elif mutant == "first_two":
+            w[0] = 2.0
+        elif mutant == "nyquist_two":
+            w[-1] = 2.0
+        else:
+            w[-1] = 1.0
+        return w
+    assert np.any(bad(shape[0]) != good(shape[0]))
+    (res2, rho2), (res2_rs, rho2_rs) = _gauss_pin_case(shape, 4, False)
+    assert abs(res2 - res2_rs) <= 1e-11 * res2_rs
+    monkeypatch.setattr(O, "half_weights", bad)
+    (res2, rho2), (res2_rs, rho2_rs) = _gauss_pin_case(shape, 4, False)
+    assert abs(rho2 - rho2_rs) > 1e-3 * rho2_rs and abs(res2 - res2_rs) > 1e-3 * res2_rs
+
+
+# --------------------------------------------------------------------------
 # decomposition: exact special case and guard truncation (Sec. 3.2)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("p,staggered", [(0, False), (16, False), (8, True)])

@@ -109,3 +109,35 @@ def test_current_enters_e_as_minus_dt_j():
 def test_courant_limit_textbook():
     assert abs(Y.courant_limit((1.0, 1.0, 1.0)) - 1 / math.sqrt(3)) < 1e-15
     assert abs(Y.courant_limit((1.0, 1e9, 1e9)) - 1.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each plausible error in the oracle fails a pin above
+# --------------------------------------------------------------------------
+def _plane_wave_error(m=(3, -2, 1), steps=20):
+    dt = 0.9 * Y.courant_limit(DX)
+    k, w, E0, B0 = _plane_wave(m, dt, 5)
+    got = Y.yee_run(_wave_fields(k, w, E0, B0, 0.0, -0.5 * dt), DX, dt, steps)
+    exp = _wave_fields(k, w, E0, B0, steps * dt, (steps - 0.5) * dt)
+    return max(np.abs(got[n] - exp[n]).max() for n in Y.E_NAMES + Y.B_NAMES)
+
+
+def _mutant(name):
+    bwd, ce, cb = Y.d_bwd, Y.curl_e, Y.curl_b
+    if name == "forward_as_backward":       # a difference taken in the wrong direction
+        return "d_fwd", lambda f, ax, du: bwd(f, ax, du)
+    if name == "curl_e_sign":               # Faraday with the wrong sign
+        return "curl_e", lambda E, dx: {k: -v for k, v in ce(E, dx).items()}
+    if name == "swapped_cell_sizes":        # dx and dz exchanged in curl B
+        return "curl_b", lambda B, dx: cb(B, (dx[2], dx[1], dx[0]))
+    if name == "half_curl_b":               # Ampere's curl term halved
+        return "curl_b", lambda B, dx: {k: 0.5 * v for k, v in cb(B, dx).items()}
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name", ["forward_as_backward", "curl_e_sign", "swapped_cell_sizes", "half_curl_b"])
+def test_plane_wave_pin_catches_planted_mistakes(monkeypatch, name):
+    assert _plane_wave_error() < 1e-11
+    attr, fn = _mutant(name)
+    monkeypatch.setattr(Y, attr, fn)
+    assert _plane_wave_error() > 1e-3
