@@ -125,7 +125,8 @@ def stage_bytes(wl, nf: int, esz: int, nout: int = 6):
     return {"A": A, "B": B, "C": C}, local
 
 
-KERNEL_SOURCES = ("psatd_kernels.cuh", "psatd_kernels_f32.cu", "small_dft.cuh", "psatd_internal.h")
+KERNEL_SOURCES = ("psatd_kernels.cuh", "psatd_kernels_f32.cu", "small_dft.cuh", "psatd_internal.h", "psatd_regfft.cuh",
+                  "psatd_regfft_f32.cu")
 
 
 def kernels_sha256() -> str:
@@ -212,7 +213,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         tuning = None
     sol = P.Solver(wl, precision=prec, gauss=gauss, device=dev, tuning=tuning,
-                   extra_flags=P.PSATD_GRID_PER_ITEM if args.grid_per_item else 0)
+                   extra_flags=(P.PSATD_GRID_PER_ITEM if args.grid_per_item else 0) |
+                   (P.PSATD_GENERIC_PLANES if args.generic_planes else 0))
     fill_solver(sol, wl, dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -275,7 +277,9 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     dom = max(stage_ms, key=stage_ms.get)
     split = P.psatd_push_launches(sol.plan) - (1 if gauss else 0) == 5
+    reg = P.psatd_plane_engine(sol.plan) == 1
     names = ({"A": "k_rows_fwd+k_cols", "B": "k_pass_b", "C": "k_cols+k_rows_inv"} if split
+             else {"A": "k_pass_a_reg", "B": "k_pass_b", "C": "k_pass_c_reg"} if reg
              else {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"})
     stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
                    "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
@@ -302,7 +306,9 @@ def run_ours(args, rank, world, local_rank):
                           "three_pass_bytes_per_step": sum(by.values()),
                           "frac_three_pass": round(sum(by.values()) / (ms_step / 1e3) / 1e9 / peak, 4)},
         "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
-        "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan), "tuning": tuning,
+        "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan),
+                    "plane_engine": "compiled-length" if P.psatd_plane_engine(sol.plan) == 1 else "generic",
+                    "tuning": tuning,
                     "persistent": not args.grid_per_item, "cuda_graph_ms_per_step": None if graph_ms is None else round(graph_ms, 4)},
         "clocks": clk.summary(),
     }
@@ -310,9 +316,14 @@ def run_ours(args, rank, world, local_rank):
     # Every step copies its sources (J, and rho with the Gauss diagnostic) as
     # global arrays of valid cells from pinned host memory, spreads them into
     # the padded boxes on the device (psatd_scatter_global: valid cells and
-    # guard images), pushes, and reads the Gauss sums back.  The copy of step
-    # k+1 runs on a second stream into a second device buffer while step k
-    # computes; read-backs use a third stream.
+    # guard images), pushes, collects the valid E and B of every subdomain
+    # into global arrays (psatd_gather_global) and copies them, with the Gauss
+    # sums, back to pinned host memory.  The upload of step k+1 runs on a
+    # second stream into a second device buffer while step k computes; the
+    # read-backs run on a third stream from two alternating device buffers.
+    # The same loop without the field read-back (fields stay resident on the
+    # device, as in a particle-in-cell code whose particle push reads them
+    # there) is reported as e2e_fields_resident.
     if not args.skip_e2e:
         names_in = ("Jx", "Jy", "Jz", "rho") if gauss else ("Jx", "Jy", "Jz")
         nx, ny, nz = wl.global_n
@@ -326,12 +337,16 @@ def run_ours(args, rank, world, local_rank):
         # push waits for an earlier step's read-back
         gh = [torch.empty(2 * len(wl.subs), dtype=torch.float64, pin_memory=True) for _ in range(ksteps)]
         gd = [torch.empty(2 * len(wl.subs), dtype=torch.float64, device=dev) for _ in range(ksteps)]
+        fdev = [{n: torch.empty((nz, ny, nx), dtype=sol.dtype, device=dev) for n in I.EB_NAMES} for _ in range(2)]
+        fhost = {n: torch.empty((nz, ny, nx), dtype=sol.dtype, pin_memory=True) for n in I.EB_NAMES}
         cs = torch.cuda.Stream(dev)
         ds = torch.cuda.Stream(dev)       # read-backs: kept off the compute stream, where they would
         pushed = [torch.cuda.Event() for _ in range(ksteps)]   # queue behind the uploads on the copy engines
         copied = [torch.cuda.Event() for _ in range(2)]
         used = [torch.cuda.Event() for _ in range(2)]
+        read = [torch.cuda.Event() for _ in range(2)]
         arenas_in = [sol.arenas[n] for n in names_in]
+        arenas_eb = [sol.arenas[n] for n in I.EB_NAMES]
 
         def upload(b):
             with torch.cuda.stream(cs):
@@ -344,8 +359,39 @@ def run_ours(args, rank, world, local_rank):
             P.psatd_scatter_global(sol.plan, [gdev[b][n] for n in names_in], arenas_in, sp)
             used[b].record(stream)
             P.psatd_push(sol.plan, sol.fields, gptr, sp)
+
+        def run_loop(fields_out):
+            for e in read:
+                e.record(ds)
+            e0, e1 = mkev(), mkev()
+            e0.record(stream)
+            cs.wait_event(e0)
+            upload(0)
+            for k in range(ksteps):
+                b = k % 2
+                if k + 1 < ksteps:
+                    if k >= 1:
+                        cs.wait_event(used[b ^ 1])
+                    upload(b ^ 1)
+                step(b, gd[k].data_ptr() if gauss else None)
+                if fields_out:
+                    stream.wait_event(read[b])          # the read-back of step k-2 has left buffer b
+                    P.psatd_gather_global(sol.plan, arenas_eb, [fdev[b][n] for n in I.EB_NAMES], sp)
+                pushed[k].record(stream)
+                ds.wait_event(pushed[k])
+                with torch.cuda.stream(ds):
+                    if gauss:
+                        gh[k].copy_(gd[k], non_blocking=True)
+                    if fields_out:
+                        for n in I.EB_NAMES:
+                            fhost[n].copy_(fdev[b][n], non_blocking=True)
+                        read[b].record(ds)
+            stream.wait_stream(ds)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / ksteps
         # warm-up of the copy path and of the pushes, outside the timed region;
-        # then the upload alone, timed, for reference
+        # then the upload, the scatter and the read-back alone, timed, for reference
         upload(0)
         upload(1)
         for b in (0, 1):
@@ -363,36 +409,32 @@ def run_ours(args, rank, world, local_rank):
         s1.record(stream)
         torch.cuda.synchronize()
         scatter_ms = s0.elapsed_time(s1)
-        e0, e1 = mkev(), mkev()
-        e0.record(stream)
-        cs.wait_event(e0)
-        upload(0)
-        for k in range(ksteps):
-            b = k % 2
-            if k + 1 < ksteps:
-                if k >= 1:
-                    cs.wait_event(used[b ^ 1])
-                upload(b ^ 1)
-            step(b, gd[k].data_ptr() if gauss else None)
-            if gauss:
-                pushed[k].record(stream)
-                ds.wait_event(pushed[k])
-                with torch.cuda.stream(ds):
-                    gh[k].copy_(gd[k], non_blocking=True)
-        stream.wait_stream(ds)
-        e1.record(stream)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(ds)
+        with torch.cuda.stream(ds):
+            for n in I.EB_NAMES:
+                fhost[n].copy_(fdev[0][n], non_blocking=True)
+        r1.record(ds)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / ksteps
-        ems = max_over_ranks(ems, world, dev)
+        readback_ms = r0.elapsed_time(r1)
+        ems = max_over_ranks(run_loop(True), world, dev)
+        rms = max_over_ranks(run_loop(False), world, dev)
+        d2h_fields = sum(t.numel() * t.element_size() for t in fhost.values())
+        d2h_gauss = gh[0].numel() * 8 if gauss else 0
         result["e2e"] = {"value": round(replica_value(valid, world, ems), 4), "unit": "Gcell-steps/s",
                          "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
-                         "d2h_bytes_per_step": gh[0].numel() * 8 if gauss else 0, "steps": ksteps,
+                         "d2h_bytes_per_step": d2h_fields + d2h_gauss, "steps": ksteps,
                          "ms_per_step": round(ems, 3), "upload_alone_ms": round(upload_ms, 3),
-                         "scatter_ms": round(scatter_ms, 3),
+                         "scatter_ms": round(scatter_ms, 3), "field_readback_alone_ms": round(readback_ms, 3),
                          "what": "per step: J (and rho) on the global grid copied from pinned host (the next "
                                  "step's copy overlapping this step), psatd_scatter_global into the padded "
-                                 "boxes, psatd_push, Gauss sums read back (on a third stream)"}
-        del host, gdev
+                                 "boxes, psatd_push, psatd_gather_global of the valid E and B, and E, B and the "
+                                 "Gauss sums copied back to pinned host (on a third stream)"}
+        result["e2e_fields_resident"] = {
+            "value": round(replica_value(valid, world, rms), 4), "unit": "Gcell-steps/s", "ms_per_step": round(rms, 3),
+            "d2h_bytes_per_step": d2h_gauss,
+            "what": "the same loop with E and B left on the device; only the Gauss sums are read back"}
+        del host, gdev, fdev, fhost
         torch.cuda.empty_cache()
     # ---- plain FP64 GPU path and FP32-vs-FP64 agreement ------------------------
     if not args.skip_plain and rank == 0:
@@ -722,6 +764,31 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 6), "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _free_port() -> int:
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def launch_replicas(args) -> int:
+    """--gpus N without a launcher: start N ranks of this script on this node
+    (one per GPU, torch.distributed.run on 127.0.0.1) and return their exit
+    status.  Each rank runs an independent replica of the workload; the
+    ranks share only the barrier and the max over ranks of the timed region."""
+    if args.impl == "ours":
+        import torch
+        have = torch.cuda.device_count()
+        if have < args.gpus:
+            print(f"bench.py: --gpus {args.gpus} but {have} GPU(s) are visible", file=sys.stderr)
+            return 2
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.run(cmd).returncode
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -740,15 +807,25 @@ def main():
     ap.add_argument("--precision", choices=["f32", "f64"], default=None, help="default: the workload's")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--grid-per-item", action="store_true", help="one CTA per work item instead of persistent grids")
+    ap.add_argument("--generic-planes", action="store_true",
+                    help="FP32: the generic plane stages instead of the compiled-length ones")
     ap.add_argument("--accuracy-steps", type=int, default=0, help="also report FP32 batched vs FP64 plain after S steps")
     ap.add_argument("--solver", choices=["psatd", "yee", "heat"], default="psatd",
                     help="yee: the FDTD comparison solver on the workload's global grid; "
                          "heat: the local-FFT heat equation on the workload's decomposition")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus < 1:
+        ap.error("--gpus must be at least 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(launch_replicas(args))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but the launcher started {world} rank(s)", file=sys.stderr)
+        sys.exit(2)
+    print(f"bench.py: rank {rank} of {world} started", file=sys.stderr, flush=True)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:

@@ -11,8 +11,11 @@
  *
  * Units: c = 1 and eps0 = 1 (Sec. 2, Eq. 2b reads D_t E = curl B - J).
  *
- * Memory model: the caller owns ALL device memory (field arenas and one
- * workspace); the library never allocates device memory.  A plan owns only
+ * Memory model: the caller owns the device memory of the solver (field arenas
+ * and one workspace); the library never allocates device memory.  The one
+ * exception is the fixed buffer behind psatd_push_static: a file-scope device
+ * array of PSATD_STATIC_WORKSPACE_BYTES (32 MiB) that every GPU which loads the
+ * library holds from module load until the process exits.  A plan owns only
  * host metadata.  psatd_push, psatd_push_profiled, psatd_exchange_guards and
  * psatd_yee_step only enqueue work on their stream: no synchronisation, no
  * allocation, no host read of device data -- so they may be captured into a
@@ -20,7 +23,8 @@
  * plan's workspace; psatd_check reports it).  A plan is not thread-safe;
  * different plans are independent.  psatd_set_workspace and psatd_set_coeffs
  * are set-up calls: they copy metadata and tables to the workspace with
- * blocking copies on the legacy default stream.
+ * blocking copies on the legacy default stream (on the plan's bound stream,
+ * synchronised, for plans made with psatd_plan).
  *
  * Errors: every function returns PSATD_OK (0) or a negative status; no C++
  * exception crosses the ABI.  psatd_last_error() gives a human-readable
@@ -89,6 +93,11 @@ extern "C" {
                                      with PSATD_STAGGERED or PSATD_GAUSS_DIAG. */
 #define PSATD_HEAT_SOURCE    0x200 /* with PSATD_HEAT: a source S in
                                      fields->J[0] (read only)                   */
+#define PSATD_GENERIC_PLANES 0x400 /* FP32: run the forward and inverse plane
+                                     stages with the generic batched kernels
+                                     even where the ones with thread-private
+                                     transforms of compile-time length apply
+                                     (see psatd_plane_engine)                  */
 #define PSATD_SPLIT_PLANES   0x80 /* split-plane schedule: the x and y transforms
                                      of the forward and inverse plane stages run
                                      as separate row and column launches (five
@@ -125,7 +134,10 @@ typedef struct {
 
 typedef struct psatd_plan_s* psatd_plan_t;
 
-/* Build a plan (host only, no CUDA call).  global_n: periodic global grid
+/* Build a plan (host only, no CUDA call) for the decomposition of Sec. 3.2
+ * (Fig. 2a): the periodic global grid cut into subdomains, each padded with
+ * ng guard cells per side, each advanced with its own local FFTs at stencil
+ * order p.  global_n: periodic global grid
  * (x, y, z).  Validated: the valid boxes tile the global grid exactly; every
  * order is 0 or even; the local x length is even, and every local length
  * (half of it along x) factors as n1*n2 with 1 <= n1, n2 <= 16, so local
@@ -134,6 +146,15 @@ typedef struct psatd_plan_s* psatd_plan_t;
  * filled from several owners). */
 int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
                       const psatd_sub* subs, int32_t nsub, int32_t flags);
+
+/* psatd_plan_create that also binds a CUDA stream to the plan (a
+ * cudaStream_t; NULL = the legacy default stream): the set-up calls
+ * psatd_set_workspace and psatd_set_coeffs then enqueue their host-to-device
+ * copies on that stream and synchronise it before returning, instead of
+ * copying on the legacy default stream.  Pushes still take their own stream
+ * argument.  Same validation and status codes as psatd_plan_create. */
+int psatd_plan(psatd_plan_t* plan, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub,
+               int32_t flags, void* cuda_stream);
 
 /* Tunable launch shapes of a plan (0 = library default for every field).
  * chunk_b: (ky,kx) modes per CTA of the z/Eq. 1 stage, 1..1024 (reduced
@@ -151,7 +172,8 @@ int psatd_plan_create_tuned(psatd_plan_t* plan, const int32_t global_n[3], const
                             int32_t nsub, int32_t flags, const psatd_tuning* tuning);
 
 /* Offset (in elements) of subdomain `sub` in every field arena, and its local
- * extents (x, y, z).  Any output pointer may be NULL. */
+ * extents (x, y, z): the padded local box of Sec. 3.2 / Fig. 2a, valid extent
+ * plus ng guard cells on each side.  Any output pointer may be NULL. */
 int psatd_layout(psatd_plan_t plan, int32_t sub, int64_t* offset_elems, int32_t local_n[3]);
 
 /* Number of elements each field arena must hold. */
@@ -218,9 +240,11 @@ int psatd_push_profiled(psatd_plan_t plan, const psatd_fields* fields, double* g
  * Eq. 1 tables into that array (stream-ordered on `stream`), then enqueues
  * the stages; it allocates nothing (no cudaMalloc, cudaFree or allocating
  * library routine).  Every call and every plan share the one array per
- * device, which keeps the last call's contents: no region of it needs to
- * start at zero, because each call rewrites everything it reads before
- * reading it.  Calls that overlap on the GPU (different streams or threads
+ * device, which keeps the last call's contents: each call rewrites
+ * everything its kernels read before they read it (the ticket counters are
+ * set to zero); only the device error word is kept across calls, for
+ * psatd_check on a plan without a workspace (it starts at zero when the
+ * library is loaded and psatd_check clears it).  Calls that overlap on the GPU (different streams or threads
  * without ordering) race on the array.  The first call on each device looks
  * the array's device address up once (with that device current); make that
  * first call before any stream capture.  A call on a device whose context was
@@ -263,7 +287,8 @@ int psatd_debug_tables(psatd_plan_t plan, double c_dt, const double dx[3], void*
  * destination of exactly one segment cell. */
 int psatd_exchange_segments(psatd_plan_t plan, int32_t* count, int32_t* segs);
 
-/* Copy every valid cell into each guard cell that images it (all 26
+/* The guard replacement of Fig. 3 step 3 (Sec. 3.2) on its own: copy every
+ * valid cell into each guard cell that images it (all 26
  * neighbour directions, periodic wrap), for E and B only (T only for
  * PSATD_HEAT plans), on `stream`. */
 int psatd_exchange_guards(psatd_plan_t plan, const psatd_fields* fields, void* stream);
@@ -286,11 +311,21 @@ const char* psatd_last_error(psatd_plan_t plan);
  * the fully descriptor-driven kernels. */
 int psatd_geometry_variant(psatd_plan_t plan, int32_t* variant);
 
+/* Which kernels run the forward (x, y) and inverse (y, x) plane stages:
+ * 1 -- FP32 kernels in which one thread transforms a whole row and two
+ * threads a whole column, with every loop unrolled for the local lengths
+ * compiled in (x: 32, 40, 48, 56, 64, 72, 88, 96, 104; y: 32, 48, 64, 80,
+ * 96; default factorisations; not with PSATD_GENERIC_PLANES or the
+ * split-plane schedule); 0 -- the generic batched plane kernels. */
+int psatd_plane_engine(psatd_plan_t plan, int32_t* engine);
+
 /* Number of kernel launches one psatd_push enqueues for this plan. */
 int psatd_push_launches(psatd_plan_t plan, int32_t* launches);
 
 /* Debug helper: synchronises the device, then returns and clears the plan's
- * device error word (in its attached workspace; PSATD_E_STATE without one).
+ * device error word (in its attached workspace; for a plan without one, in
+ * the static workspace of its last psatd_push_static -- a word shared by all
+ * static pushes on that device; PSATD_E_STATE if the plan has neither).
  * Bits: PSATD_CHECK_ITEM -- a work item was decoded outside its subdomain's
  * item range (the workspace's descriptors were overwritten);
  * PSATD_CHECK_TICKETS -- a persistent launch drew more tickets than it
@@ -298,6 +333,8 @@ int psatd_push_launches(psatd_plan_t plan, int32_t* launches);
  * are then undefined).  Kernels set bits and carry on; they never wait. */
 #define PSATD_CHECK_ITEM     0x1
 #define PSATD_CHECK_TICKETS  0x2
+#define PSATD_CHECK_WAIT     0x4  /* a bounded wait for a bulk copy into shared
+                                     memory gave up; the CTA stopped early    */
 int psatd_check(psatd_plan_t plan, int32_t* error_bits);
 
 #ifdef __cplusplus

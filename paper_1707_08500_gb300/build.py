@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpsatd.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ("psatd_kernels_f32.cu", "psatd_kernels_f64.cu", "psatd_plan.cpp", "psatd_static.cu", "fdtd_yee.cu", "psatd_io.cu")
+SOURCES = ("psatd_kernels_f32.cu", "psatd_kernels_f64.cu", "psatd_regfft_f32.cu", "psatd_plan.cpp", "psatd_static.cu",
+           "fdtd_yee.cu", "psatd_io.cu")
 
 
 def nvcc() -> str:

@@ -35,6 +35,16 @@ constexpr int pad_field_stride(int lz, int m, int csz) {
 
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
+// FP32 plane stages with thread-private transforms of compile-time length
+// (psatd_regfft.cuh): the local x and y lengths they are compiled for, the
+// CTA size, and the shared-memory row pitch of pass A (complex elements: at
+// least Lx/2+1 and = 2 mod 4, so rows are 16-byte aligned and eight
+// consecutive rows start on distinct 16-byte bank groups).
+constexpr int kRegThreads = 128;
+constexpr int kRegX2[] = {32, 40, 48, 56, 64, 72, 88, 96, 104};
+constexpr int kRegY[] = {32, 48, 64, 80, 96};
+constexpr int reg_pitch(int lxh) { return lxh + ((2 - lxh % 4) + 4) % 4; }
+
 // Cubic local boxes (side L, ng guards, pass-B chunk M, default splits) that
 // have kernels compiled with their geometry fixed at compile time.
 struct FixedGeo { int L, ng, M; };

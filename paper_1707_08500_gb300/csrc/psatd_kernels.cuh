@@ -999,7 +999,7 @@ struct LaunchCache {
     int dev, smem_set, smem_occ, per_sm, nsm;
 };
 
-static cudaError_t launch_shape(const void* fn, int smem, bool persistent, int* resident) {
+static cudaError_t launch_shape(const void* fn, int smem, bool persistent, int* resident, int threads = kThreads) {
     static std::mutex mu;
     static LaunchCache cache[128];
     static int ncache = 0;
@@ -1018,7 +1018,7 @@ static cudaError_t launch_shape(const void* fn, int smem, bool persistent, int* 
         c->smem_set = smem;
     }
     if (persistent && smem != c->smem_occ) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, fn, threads, smem)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         c->smem_occ = smem;
     }
@@ -1029,13 +1029,13 @@ static cudaError_t launch_shape(const void* fn, int smem, bool persistent, int* 
 // One launch of kernel k: persistent (as many CTAs as can be resident, each
 // drawing work items from the ticket counter) or one CTA per item.
 template <typename T>
-static cudaError_t launch_kernel(void (*k)(Args<T>), const Args<T>& a, int smem, cudaStream_t st) {
+static cudaError_t launch_kernel(void (*k)(Args<T>), const Args<T>& a, int smem, cudaStream_t st, int threads = kThreads) {
     int resident = 0;
-    cudaError_t e = launch_shape((const void*)k, smem, a.persistent != 0, &resident);
+    cudaError_t e = launch_shape((const void*)k, smem, a.persistent != 0, &resident, threads);
     if (e != cudaSuccess) return e;
     unsigned grid = grid_for(a.nitems);
     if (a.persistent) grid = grid_for(a.nitems < resident ? a.nitems : resident);
-    k<<<grid, kThreads, smem, st>>>(a);
+    k<<<grid, threads, smem, st>>>(a);
     return cudaPeekAtLastError();
 }
 

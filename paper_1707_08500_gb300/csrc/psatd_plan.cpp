@@ -21,6 +21,7 @@ namespace psatd {
 cudaError_t launch_stage_f32(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
 cudaError_t launch_stage_f64(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
 cudaError_t launch_gauss_reduce(const void* subs, int nsub, const double* part, double* out, cudaStream_t st);
+cudaError_t launch_stage_reg(int stage, const LaunchCommon& c, int64_t i0, int64_t n, int smem, cudaStream_t s);
 }  // namespace psatd
 
 using namespace psatd;
@@ -149,16 +150,21 @@ struct psatd_plan_s {
     int variant = -1;                  // compile-time geometry variant, or -1
     int smemA = 0, smemB = 0, smemC = 0, smemR = 0, smemK = 0;
     bool split = false;                // split-plane schedule (row and column launches)
+    bool reg = false;                  // FP32 plane stages with compile-time-length transforms
+    int smemAreg = 0, smemCreg = 0;
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_work = 0, off_spec = 0, ws_need = 0;
     size_t off_io = 0, off_io_map = 0;
     int64_t spec_elems = 0;
     char* ws = nullptr;
     size_t ws_size = 0;
+    cudaStream_t setup_stream = nullptr;   // stream of the set-up copies (psatd_plan), or the legacy stream
+    bool bound_stream = false;
     bool coeffs = false;
     std::string err;
     // host images for pushes into library-owned device memory (push_into)
     bool img_valid = false;
+    char* static_base = nullptr;       // static workspace of the last psatd_push_static on this plan
     double img_c_dt = 0, img_dx[3] = {0, 0, 0};
     std::vector<char> img_tw, img_tab, img_tabc;
 };
@@ -326,6 +332,16 @@ int psatd_plan_create(psatd_plan_t* out, const int32_t global_n[3], const psatd_
     return psatd_plan_create_tuned(out, global_n, subs, nsub, flags, nullptr);
 }
 
+int psatd_plan(psatd_plan_t* out, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub, int32_t flags,
+               void* cuda_stream) {
+    const int r = psatd_plan_create_tuned(out, global_n, subs, nsub, flags, nullptr);
+    if (r == PSATD_OK) {
+        (*out)->setup_stream = static_cast<cudaStream_t>(cuda_stream);
+        (*out)->bound_stream = true;
+    }
+    return r;
+}
+
 int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const psatd_sub* subs, int32_t nsub,
                             int32_t flags, const psatd_tuning* tuning) {
     if (!out || !global_n || !subs || nsub <= 0) return PSATD_E_ARG;
@@ -341,7 +357,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
     if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D |
-                  PSATD_SPLIT_PLANES | PSATD_HEAT | PSATD_HEAT_SOURCE))
+                  PSATD_SPLIT_PLANES | PSATD_HEAT | PSATD_HEAT_SOURCE | PSATD_GENERIC_PLANES))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -568,6 +584,21 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     }
     if (p->smemB > kPlaneSmemMax || (p->split && std::max(p->smemR, p->smemK) > kPlaneSmemMax))
         return bad(PSATD_E_UNSUPPORTED, "a stage's tile does not fit in shared memory");
+    // FP32 plane stages with compile-time-length transforms: every local x
+    // and y length compiled in, default factorisations, at most 128 rows and
+    // 64 half-spectrum columns (one thread per row, two per column)
+    if (!p->f64 && !p->split && !(flags & PSATD_GENERIC_PLANES)) {
+        auto listed = [](const int* l, int n, int v) { for (int i = 0; i < n; ++i) if (l[i] == v) return true; return false; };
+        bool ok = true;
+        for (const SubDesc& d : p->desc) {
+            ok = ok && listed(kRegX2, int(sizeof(kRegX2) / sizeof(int)), d.L[0]) &&
+                 listed(kRegY, int(sizeof(kRegY) / sizeof(int)), d.L[1]) && d.ax.f1 == split_first(d.L[0] / 2) &&
+                 d.ay.f1 == split_first(d.L[1]) && d.lxh <= kRegThreads / 2 && d.L[1] <= kRegThreads;
+            p->smemAreg = std::max(p->smemAreg, d.L[1] * reg_pitch(d.lxh) * 8);
+            p->smemCreg = std::max(p->smemCreg, d.q * 8);
+        }
+        p->reg = ok && p->smemAreg <= kPlaneSmemMax && p->smemCreg <= kPlaneSmemMax;
+    }
     // --- exchange segments (source valid box -> destination local box) ----------
     for (int s = 0; s < nsub; ++s) {
         p->desc[s].seg_begin = int(p->segs.size());
@@ -687,6 +718,12 @@ int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
     return PSATD_OK;
 }
 
+int psatd_plane_engine(psatd_plan_t p, int32_t* engine) {
+    if (!p || !engine) return PSATD_E_ARG;
+    *engine = p->reg ? 1 : 0;
+    return PSATD_OK;
+}
+
 static int io_call(psatd_plan_s* p, bool scatter, const void* const* src, void* const* dst, int32_t nfields,
                    void* stream) {
     if (!p || !src || !dst) return PSATD_E_ARG;
@@ -753,11 +790,13 @@ int psatd_exchange_segments(psatd_plan_t p, int32_t* count, int32_t* segs) {
 
 int psatd_check(psatd_plan_t p, int32_t* error_bits) {
     if (!p || !error_bits) return PSATD_E_ARG;
-    if (!p->ws) return fail(p, PSATD_E_STATE, "set the workspace first");
+    // the attached workspace, else the static workspace of psatd_push_static
+    char* base = p->ws ? p->ws : p->static_base;
+    if (!base) return fail(p, PSATD_E_STATE, "set the workspace first");
     cudaError_t e = cudaDeviceSynchronize();
     unsigned int w = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&w, p->ws + p->off_work + 7 * sizeof(unsigned long long), sizeof(w), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_work + 7 * sizeof(unsigned long long), 0, sizeof(w));
+    if (e == cudaSuccess) e = cudaMemcpy(&w, base + p->off_work + 7 * sizeof(unsigned long long), sizeof(w), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(base + p->off_work + 7 * sizeof(unsigned long long), 0, sizeof(w));
     if (e != cudaSuccess) return cuda_fail(p, e, "read the device error word");
     *error_bits = int32_t(w);
     return PSATD_OK;
@@ -772,6 +811,21 @@ int psatd_push_launches(psatd_plan_t p, int32_t* n) {
     return PSATD_OK;
 }
 
+// Host-to-device copy of a set-up call: blocking on the legacy default
+// stream, or enqueued on the plan's bound stream (psatd_plan) and that stream
+// synchronised.
+static cudaError_t setup_copy(psatd_plan_s* p, void* dst, const void* src, size_t n) {
+    if (!p->bound_stream) return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, p->setup_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(p->setup_stream) : e;
+}
+
+static cudaError_t setup_zero(psatd_plan_s* p, void* dst, size_t n) {
+    if (!p->bound_stream) return cudaMemset(dst, 0, n);
+    cudaError_t e = cudaMemsetAsync(dst, 0, n, p->setup_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(p->setup_stream) : e;
+}
+
 int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
     if (!p || !dev) return PSATD_E_ARG;
     if (reinterpret_cast<uintptr_t>(dev) % 256) return fail(p, PSATD_E_ARG, "workspace must be 256-byte aligned");
@@ -779,24 +833,23 @@ int psatd_set_workspace(psatd_plan_t p, void* dev, size_t bytes) {
     p->ws = static_cast<char*>(dev);
     p->ws_size = bytes;
     p->coeffs = false;
-    cudaError_t e = cudaMemcpy(p->ws + p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = setup_copy(p, p->ws + p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size());
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy descriptors"); }
     if (!p->segs.empty()) {
-        e = cudaMemcpy(p->ws + p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size(), cudaMemcpyHostToDevice);
+        e = setup_copy(p, p->ws + p->off_seg, p->segs.data(), sizeof(Segment) * p->segs.size());
         if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy segments"); }
     }
-    e = cudaMemcpy(p->ws + p->off_io, p->io.data(), sizeof(IoDesc) * p->io.size(), cudaMemcpyHostToDevice);
+    e = setup_copy(p, p->ws + p->off_io, p->io.data(), sizeof(IoDesc) * p->io.size());
     if (e == cudaSuccess)
-        e = cudaMemcpy(p->ws + p->off_io_map, p->io_plane_sub.data(), sizeof(int) * p->io_plane_sub.size(),
-                       cudaMemcpyHostToDevice);
+        e = setup_copy(p, p->ws + p->off_io_map, p->io_plane_sub.data(), sizeof(int) * p->io_plane_sub.size());
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy the copy descriptors"); }
     {
         const std::vector<char> tw = twiddle_image(p);
-        e = cudaMemcpy(p->ws + p->off_tw, tw.data(), tw.size(), cudaMemcpyHostToDevice);
+        e = setup_copy(p, p->ws + p->off_tw, tw.data(), tw.size());
     }
     // the persistent launches' ticket counters and the error word (the last
     // slot) start at zero (each launch returns its counter to zero when it ends)
-    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_work, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = setup_zero(p, p->ws + p->off_work, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) { p->ws = nullptr; return cuda_fail(p, e, "copy twiddles"); }
     return PSATD_OK;
 }
@@ -807,9 +860,9 @@ int psatd_set_coeffs(psatd_plan_t p, double c_dt, const double dx[3]) {
     if (!(c_dt == c_dt) || !(dx[0] > 0 && dx[1] > 0 && dx[2] > 0)) return fail(p, PSATD_E_ARG, "bad c_dt or dx");
     std::vector<char> tab, tabc;
     table_images(p, c_dt, dx, tab, tabc);
-    cudaError_t e = cudaMemcpy(p->ws + p->off_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = setup_copy(p, p->ws + p->off_tab, tab.data(), tab.size());
     if (e == cudaSuccess && p->n_tabc)
-        e = cudaMemcpy(p->ws + p->off_tabc, tabc.data(), tabc.size(), cudaMemcpyHostToDevice);
+        e = setup_copy(p, p->ws + p->off_tabc, tabc.data(), tabc.size());
     if (e != cudaSuccess) return cuda_fail(p, e, "copy coefficient tables");
     p->coeffs = true;
     return PSATD_OK;
@@ -911,7 +964,9 @@ static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaS
     // of each (n < 0: every item of the stage)
     struct Range { int64_t a0, an, a20, a2n, b0, bn, c10, c1n, c0, cn; };
     auto run = [&](const Range& r) -> int {
-        if (!p->split) {
+        if (p->reg) {
+            if ((e = launch_stage_reg(0, c, r.a0, r.an, p->smemAreg, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
+        } else if (!p->split) {
             if ((e = stage(p, 0, c, r.a0, r.an, p->smemA, s)) != cudaSuccess) return cuda_fail(p, e, "pass A launch");
         } else {
             if ((e = stage(p, 4, c, r.a0, r.an, p->smemR, s)) != cudaSuccess) return cuda_fail(p, e, "x rows launch");
@@ -920,7 +975,9 @@ static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaS
         if (!p->plain && (e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
         if ((e = stage(p, p->heat ? 8 : 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
         if (!p->plain && (e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
-        if (!p->split) {
+        if (p->reg) {
+            if ((e = launch_stage_reg(2, c, r.c0, r.cn, p->smemCreg, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
+        } else if (!p->split) {
             if ((e = stage(p, 2, c, r.c0, r.cn, p->smemC, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");
         } else {
             if ((e = stage(p, 6, c, r.c10, r.c1n, p->smemK, s)) != cudaSuccess) return cuda_fail(p, e, "y columns launch");
@@ -996,7 +1053,9 @@ int push_into(psatd_plan_s* p, char* base, size_t cap, double c_dt, const double
         for (int a = 0; a < 3; ++a) p->img_dx[a] = dx[a];
         p->img_valid = true;
     }
-    static const unsigned long long zero_work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // the ticket counters start at zero; the error word (slot 7) is kept, so
+    // that psatd_check can report what earlier static pushes recorded
+    static const unsigned long long zero_work[7] = {0, 0, 0, 0, 0, 0, 0};
     struct Part { size_t off; const void* src; size_t n; } parts[] = {
         {p->off_work, zero_work, sizeof(zero_work)},
         {p->off_desc, p->desc.data(), sizeof(SubDesc) * p->desc.size()},
@@ -1010,6 +1069,7 @@ int push_into(psatd_plan_s* p, char* base, size_t cap, double c_dt, const double
         cudaError_t e = cudaMemcpyAsync(base + q.off, q.src, q.n, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(p, e, "copy plan image to the static workspace");
     }
+    p->static_base = base;
     return launch_push(p, common_at(p, base, f), gauss_dev, s, nullptr);
 }
 

@@ -28,16 +28,17 @@ PSATD_2D = 0x40
 PSATD_SPLIT_PLANES = 0x80
 PSATD_HEAT = 0x100
 PSATD_HEAT_SOURCE = 0x200
+PSATD_GENERIC_PLANES = 0x400
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}
 
-EXPORTS = ("psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
+EXPORTS = ("psatd_plan", "psatd_plan_create", "psatd_layout", "psatd_arena_elems", "psatd_workspace_bytes",
            "psatd_set_workspace", "psatd_set_coeffs", "psatd_push", "psatd_exchange_guards",
            "psatd_destroy", "psatd_status_string", "psatd_last_error", "psatd_push_launches",
            "psatd_push_profiled", "psatd_plan_create_tuned", "psatd_push_static", "psatd_geometry_variant",
            "psatd_yee_step", "psatd_yee_launches", "psatd_check", "psatd_scatter_global",
-           "psatd_gather_global", "psatd_exchange_segments", "psatd_debug_tables")
+           "psatd_gather_global", "psatd_exchange_segments", "psatd_debug_tables", "psatd_plane_engine")
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -74,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         P, I32, I64, VP = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         L.psatd_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(SubT), I32, I32]
+        L.psatd_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(SubT), I32, I32, VP]
         L.psatd_plan_create_tuned.argtypes = [ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(SubT), I32, I32,
                                               ctypes.POINTER(TuningT)]
         L.psatd_layout.argtypes = [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32)]
@@ -93,6 +95,7 @@ def lib() -> ctypes.CDLL:
         L.psatd_last_error.restype = ctypes.c_char_p
         L.psatd_push_launches.argtypes = [P, ctypes.POINTER(I32)]
         L.psatd_geometry_variant.argtypes = [P, ctypes.POINTER(I32)]
+        L.psatd_plane_engine.argtypes = [P, ctypes.POINTER(I32)]
         for name in EXPORTS:
             if name not in ("psatd_status_string", "psatd_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -124,6 +127,22 @@ def psatd_plan_create(global_n: Sequence[int], subs: Sequence, flags: int, tunin
         t.chunk_b = int(tuning.get("chunk_b", 0))
         t.f1[:] = [int(v) for v in tuning.get("f1", (0, 0, 0))]
         code = lib().psatd_plan_create_tuned(ctypes.byref(h), g, arr, len(subs), flags, ctypes.byref(t))
+    if code != 0:
+        raise PsatdError(code, lib().psatd_status_string(code).decode())
+    return h
+
+
+def psatd_plan(global_n: Sequence[int], subs: Sequence, flags: int, stream: Optional[int] = None) -> ctypes.c_void_p:
+    """psatd_plan_create with a bound set-up stream (raw cudaStream_t or None)."""
+    arr = (SubT * max(len(subs), 1))()
+    for i, s in enumerate(subs):
+        arr[i].lo[:] = list(s.lo)
+        arr[i].n[:] = list(s.n)
+        arr[i].ng = s.ng
+        arr[i].order = s.p
+    g = (ctypes.c_int32 * 3)(*global_n)
+    h = ctypes.c_void_p()
+    code = lib().psatd_plan(ctypes.byref(h), g, arr, len(subs), flags, ctypes.c_void_p(stream or 0))
     if code != 0:
         raise PsatdError(code, lib().psatd_status_string(code).decode())
     return h
@@ -265,6 +284,12 @@ def psatd_push_launches(plan) -> int:
 def psatd_geometry_variant(plan) -> int:
     n = ctypes.c_int32()
     _check(lib().psatd_geometry_variant(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def psatd_plane_engine(plan) -> int:
+    n = ctypes.c_int32()
+    _check(lib().psatd_plane_engine(plan, ctypes.byref(n)), plan)
     return n.value
 
 

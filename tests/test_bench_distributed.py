@@ -86,3 +86,35 @@ def test_reference_arm_prints_one_json_line(solver):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_gpus_flag_starts_that_many_ranks():
+    """bench.py --gpus 2 started without a launcher starts two ranks itself
+    (torch.distributed.run on 127.0.0.1); on the reference arm rank 0 alone
+    prints the JSON line, with n_gpus = 2, and the other rank exits 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3", "--ref-subs", "1", "--workload", "plain32"],
+                       capture_output=True, text=True, timeout=600, cwd=root, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    started = sorted(l for l in r.stderr.splitlines() if "started" in l and l.startswith("bench.py: rank"))
+    assert started == ["bench.py: rank 0 of 2 started", "bench.py: rank 1 of 2 started"], r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    assert json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_rank_count_mismatch_fails_loudly():
+    """Under a launcher whose world size differs from --gpus the bench refuses
+    to run instead of mislabelling its line."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       capture_output=True, text=True, timeout=300, cwd=root, env=env)
+    assert r.returncode == 2 and "--gpus 2" in r.stderr

@@ -97,7 +97,7 @@ def test_plan_rejects_bad_input(P, case, code):
     elif case == "no_subdomains":
         subs = []
     elif case == "unknown_flag":
-        flags = P.PSATD_F32 | 0x400
+        flags = P.PSATD_F32 | 0x4000
     elif case == "negative_guard":
         subs = [I.Sub(s.lo, s.n, -1, 8) for s in subs]
     elif case == "empty_global":
@@ -388,3 +388,27 @@ def test_coefficient_tables_match_the_oracle(P, p_order, staggered):
     for t, w in enumerate(want):
         got = img[t * NM:(t + 1) * NM].reshape(L[2], L[1], lxh)
         np.testing.assert_allclose(got, w, rtol=1e-12, atol=1e-15 * (1.0 if t < 6 else 10.0), err_msg=str(t))
+
+
+def test_compiled_length_plane_engine_selection(P):
+    """FP32 plans whose local x and y lengths are all compiled in take the
+    plane stages with thread-private transforms (engine 1); FP64, odd or
+    uncompiled lengths, non-default factorisations, the split-plane schedule
+    and PSATD_GENERIC_PLANES take the generic ones (engine 0)."""
+    cases = [("mirror1024", P.PSATD_F32, None, 1), ("broadband256", P.PSATD_F32, None, 1),
+             ("uneven48", P.PSATD_F32, None, 1), ("broadband2d", P.PSATD_F32 | P.PSATD_2D, None, 1),
+             ("mirror1024", P.PSATD_F64, None, 0), ("broadband256", P.PSATD_F32 | P.PSATD_GENERIC_PLANES, None, 0),
+             ("broadband256", P.PSATD_F32 | P.PSATD_SPLIT_PLANES, None, 0),
+             ("broadband256", P.PSATD_F32, {"chunk_b": 0, "f1": [6, 0, 0]}, 0),
+             ("broadband256", P.PSATD_F32, {"chunk_b": 0, "f1": [0, 0, 6]}, 1)]
+    for name, flags, tuning, want in cases:
+        wl = I.workload(name)
+        h = P.psatd_plan_create(wl.global_n, wl.subs, flags, tuning)
+        try:
+            assert P.psatd_plane_engine(h) == want, (name, flags, tuning)
+        finally:
+            P.psatd_destroy(h)
+    subs = I.tensor_decomposition([12, 20], [14, 13], [18, 17], 4, 8)     # odd local lengths
+    h = P.psatd_plan_create((32, 27, 35), subs, P.PSATD_F32)
+    assert P.psatd_plane_engine(h) == 0
+    P.psatd_destroy(h)
