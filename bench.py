@@ -277,10 +277,12 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     dom = max(stage_ms, key=stage_ms.get)
     split = P.psatd_push_launches(sol.plan) - (1 if gauss else 0) == 5
-    reg = P.psatd_plane_engine(sol.plan) == 1
+    engine = P.psatd_plane_engine(sol.plan)
     names = ({"A": "k_rows_fwd+k_cols", "B": "k_pass_b", "C": "k_cols+k_rows_inv"} if split
-             else {"A": "k_pass_a_reg", "B": "k_pass_b", "C": "k_pass_c_reg"} if reg
+             else {"A": "k_pass_a_reg", "B": "k_pass_b", "C": "k_pass_c_reg"} if engine & 1
              else {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"})
+    if engine & 2:
+        names["B"] = "k_pass_b_reg"
     stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
                    "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
     achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
@@ -307,7 +309,8 @@ def run_ours(args, rank, world, local_rank):
                           "frac_three_pass": round(sum(by.values()) / (ms_step / 1e3) / 1e9 / peak, 4)},
         "gpu_launches": args.steps * P.psatd_push_launches(sol.plan),
         "kernels": {"geometry_variant": P.psatd_geometry_variant(sol.plan),
-                    "plane_engine": "compiled-length" if P.psatd_plane_engine(sol.plan) == 1 else "generic",
+                    "engine": {"planes": "compiled-length" if engine & 1 else "generic",
+                               "z_eq1": "compiled-length" if engine & 2 else "generic"},
                     "tuning": tuning,
                     "persistent": not args.grid_per_item, "cuda_graph_ms_per_step": None if graph_ms is None else round(graph_ms, 4)},
         "clocks": clk.summary(),
@@ -452,22 +455,40 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / nst
+        launches = P.psatd_push_launches(s64.plan)
+        del s64
+        torch.cuda.empty_cache()
+        # the FP32 batched path against FP64 after S steps of each (the FP64
+        # reference runs batched: the same arithmetic as the plain FP64 path,
+        # one launch per stage, so S = 100 fits in the run)
+        S = args.plain_accuracy_steps
         s32 = P.Solver(wl, precision="f32", gauss=gauss, device=dev)
         fill_solver(s32, wl, dev)
-        for _ in range(1 + nst):
+        for _ in range(S):
             s32.push(sp)
         torch.cuda.synchronize()
+        keep = {n: s32.arenas[n].clone() for n in I.EB_NAMES}
+        del s32
+        torch.cuda.empty_cache()
+        s64 = P.Solver(wl, precision="f64", gauss=gauss, device=dev)
+        fill_solver(s64, wl, dev)
+        for _ in range(S):
+            s64.push(sp)
+        torch.cuda.synchronize()
         num = den = 0.0
+        comp = {}
         for n in I.EB_NAMES:
-            d = (s32.arenas[n].double() - s64.arenas[n])
+            d = (keep[n].double() - s64.arenas[n])
             num += float((d * d).sum())
             den += float((s64.arenas[n] * s64.arenas[n]).sum())
+            comp[n] = float(f"{float(d.abs().max() / s64.arenas[n].abs().max()):.3e}")
         pv = valid / (pms / 1e3) / 1e9
         result["plain_f64"] = {"value": round(pv, 5), "unit": "Gcell-steps/s", "ms_per_step": round(pms, 2),
                                "speedup_of_batched_f32": round(value / world / pv, 2),
-                               "f32_vs_f64_rel_l2_after_3_steps": float(f"{math.sqrt(num / den):.3e}"),
-                               "launches_per_step": P.psatd_push_launches(s64.plan)}
-        del s64, s32
+                               f"f32_vs_f64_rel_l2_after_{S}_steps": float(f"{math.sqrt(num / den):.3e}"),
+                               f"f32_vs_f64_max_rel_per_component_after_{S}_steps": comp,
+                               "launches_per_step": launches}
+        del s64, keep
         torch.cuda.empty_cache()
     # ---- FP32 batched vs FP64 plain over S steps (reported accuracy) -----------
     if args.accuracy_steps and rank == 0:
@@ -490,10 +511,63 @@ def run_ours(args, rank, world, local_rank):
         result["accuracy"] = {"steps": args.accuracy_steps, "f32_batched_vs_f64_plain_rel_l2": float(f"{math.sqrt(num / den):.3e}")}
         del a64, keep
         torch.cuda.empty_cache()
+    # ---- the precision and batching workloads, timed the same way --------------
+    if args.extra_workloads and rank == 0:
+        sol = None
+        torch.cuda.empty_cache()
+        result["workloads"] = {w: time_workload(w, args, dev, peak) for w in args.extra_workloads.split(",") if w}
     # ---- CPU oracle baseline (rank 0, N = 1 only) -------------------------------
     if not args.skip_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_oracle_sample(wl, args.cpu_budget)
     return result
+
+
+def time_workload(name, args, dev, peak):
+    """One more workload through the same plan and timing as the main line
+    (FP32 batched with the Gauss diagnostic, persistent grids, default
+    shapes): W warm-up steps, then K steps with CUDA events at the stage
+    boundaries.  Returns throughput and, per stage, the algorithmic bytes
+    over the mean stage time as a fraction of the HBM peak."""
+    import torch
+    from paper_1707_08500_gb300 import inputs as I
+    from paper_1707_08500_gb300 import psatd as P
+    wl = I.workload(name)
+    prec = "f32" if wl.precision == "f32" else "f64"
+    sol = P.Solver(wl, precision=prec, gauss=True, device=dev)
+    fill_solver(sol, wl, dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    for _ in range(args.warmup):
+        sol.push(sp)
+    K = max(args.steps, 10)
+    def mkev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)          # recorded once here, so torch treats it as recorded
+        return e
+    evs = [[mkev() for _ in range(4)] for _ in range(K)]
+    t0, t1 = mkev(), mkev()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(K):
+        P.psatd_push_profiled(sol.plan, sol.fields, sol.gauss_out.data_ptr(), sp, [e.cuda_event for e in evs[k]])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / K
+    stage_ms = {st: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)) / K for i, st in enumerate("ABC")}
+    by, local = stage_bytes(wl, 10, 4 if prec == "f32" else 8)
+    engine = P.psatd_plane_engine(sol.plan)
+    names = {"A": "k_pass_a_reg" if engine & 1 else "k_pass_a", "B": "k_pass_b_reg" if engine & 2 else "k_pass_b",
+             "C": "k_pass_c_reg" if engine & 1 else "k_pass_c"}
+    stages = {st: {"kernel": names[st], "ms": round(stage_ms[st], 4),
+                   "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1),
+                   "frac": round(by[st] / (stage_ms[st] / 1e3) / 1e9 / peak, 4)} for st in "ABC"}
+    dom = max(stage_ms, key=stage_ms.get)
+    del sol
+    torch.cuda.empty_cache()
+    return {"value": round(wl.valid_cells / (ms / 1e3) / 1e9, 4), "unit": "Gcell-steps/s", "ms_per_step": round(ms, 4),
+            "steps": K, "warmup": args.warmup, "dtype": prec, "global_n": list(wl.global_n),
+            "subdomains": len(wl.subs), "stages": stages,
+            "dominant": {"kernel": names[dom], "frac": stages[dom]["frac"], "peak_gbs": peak}}
 
 
 YEE_METRIC = "Gcell-steps/s of the Yee FDTD step (Eqs. 2a/2b), FP32; % HBM roof"
@@ -810,6 +884,10 @@ def main():
     ap.add_argument("--generic-planes", action="store_true",
                     help="FP32: the generic plane stages instead of the compiled-length ones")
     ap.add_argument("--accuracy-steps", type=int, default=0, help="also report FP32 batched vs FP64 plain after S steps")
+    ap.add_argument("--plain-accuracy-steps", type=int, default=100,
+                    help="steps of the FP32-vs-FP64 comparison reported with the plain FP64 path")
+    ap.add_argument("--extra-workloads", default="broadband256,uneven48",
+                    help="comma-separated workloads also timed after the main one (empty: none)")
     ap.add_argument("--solver", choices=["psatd", "yee", "heat"], default="psatd",
                     help="yee: the FDTD comparison solver on the workload's global grid; "
                          "heat: the local-FFT heat equation on the workload's decomposition")

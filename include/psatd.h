@@ -48,8 +48,8 @@ extern "C" {
                                     guard wider than supported, bad extent    */
 #define PSATD_E_NOMEM        -3  /* workspace smaller than psatd_workspace_bytes */
 #define PSATD_E_CUDA         -4  /* a CUDA runtime call or launch failed       */
-#define PSATD_E_UNSUPPORTED  -5  /* local length not a product of two factors
-                                    in 1..16, or odd local x length           */
+#define PSATD_E_UNSUPPORTED  -5  /* local length not a product of two or three
+                                    factors in 1..16, or odd local x length   */
 #define PSATD_E_STATE        -6  /* workspace or coefficients not set yet      */
 #define PSATD_E_TIMEOUT      -7  /* reserved: a bounded device wait gave up    */
 
@@ -93,11 +93,19 @@ extern "C" {
                                      with PSATD_STAGGERED or PSATD_GAUSS_DIAG. */
 #define PSATD_HEAT_SOURCE    0x200 /* with PSATD_HEAT: a source S in
                                      fields->J[0] (read only)                   */
-#define PSATD_GENERIC_PLANES 0x400 /* FP32: run the forward and inverse plane
-                                     stages with the generic batched kernels
-                                     even where the ones with thread-private
-                                     transforms of compile-time length apply
-                                     (see psatd_plane_engine)                  */
+#define PSATD_GENERIC_PLANES 0x400 /* FP32: run every stage with the generic
+                                     batched kernels even where the ones with
+                                     thread-private transforms of compile-time
+                                     length apply (see psatd_plane_engine)     */
+#define PSATD_PACKED_Z       0x800 /* FP32: the z/Eq. 1 stage with one thread per
+                                     mode pair and quarter of its z DFTs, the
+                                     two modes of a pair on packed FP32x2
+                                     lanes, for the local z lengths compiled in
+                                     (see psatd_plane_engine).  It executes
+                                     fewer instructions than the default
+                                     batched z/Eq. 1 kernel but holds fewer
+                                     warps per SM, which on 96^3 boxes makes
+                                     it slower; opt-in                        */
 #define PSATD_SPLIT_PLANES   0x80 /* split-plane schedule: the x and y transforms
                                      of the forward and inverse plane stages run
                                      as separate row and column launches (five
@@ -140,8 +148,10 @@ typedef struct psatd_plan_s* psatd_plan_t;
  * order p.  global_n: periodic global grid
  * (x, y, z).  Validated: the valid boxes tile the global grid exactly; every
  * order is 0 or even; the local x length is even, and every local length
- * (half of it along x) factors as n1*n2 with 1 <= n1, n2 <= 16, so local
- * boxes reach 512 x 256 x 256; flags hold exactly one of PSATD_F32 /
+ * (half of it along x) factors as n1*n2 with 1 <= n1, n2 <= 16, or else as
+ * n1*n2*n3 with 2 <= n1, n2, n3 <= 16 (so any length whose prime factors are
+ * 2, 3, 5, 7, 11 and 13 with at most three factors per 16, up to 4096; local
+ * x up to 8192); flags hold exactly one of PSATD_F32 /
  * PSATD_F64.  Guard widths may exceed a neighbour's width (the guard is then
  * filled from several owners). */
 int psatd_plan_create(psatd_plan_t* plan, const int32_t global_n[3],
@@ -161,7 +171,7 @@ int psatd_plan(psatd_plan_t* plan, const int32_t global_n[3], const psatd_sub* s
  * until the stage's tile fits in shared memory);
  * f1[3]: first factor of the two-stage FFT of the x (half length), y and z
  * axes; used for every subdomain whose length it divides with both factors
- * in 1..16, ignored otherwise. */
+ * in 1..16, ignored otherwise (and for axes split in three factors). */
 typedef struct {
     int32_t chunk_b;
     int32_t f1[3];
@@ -311,12 +321,17 @@ const char* psatd_last_error(psatd_plan_t plan);
  * the fully descriptor-driven kernels. */
 int psatd_geometry_variant(psatd_plan_t plan, int32_t* variant);
 
-/* Which kernels run the forward (x, y) and inverse (y, x) plane stages:
- * 1 -- FP32 kernels in which one thread transforms a whole row and two
- * threads a whole column, with every loop unrolled for the local lengths
- * compiled in (x: 32, 40, 48, 56, 64, 72, 88, 96, 104; y: 32, 48, 64, 80,
- * 96; default factorisations; not with PSATD_GENERIC_PLANES or the
- * split-plane schedule); 0 -- the generic batched plane kernels. */
+/* Which kernels run the stages, as bits: 1 -- the forward (x, y) and inverse
+ * (y, x) plane stages are FP32 kernels in which one thread transforms a whole
+ * row and a thread a column pair, with the DFT bodies unrolled for the local
+ * lengths compiled in (x: 32, 40, 48, 56, 64, 72, 88, 96, 104; y: 32, 48, 64,
+ * 80, 96; default factorisations; not with the split-plane schedule);
+ * 2 -- the z/Eq. 1 stage is the packed FP32 kernel (PSATD_PACKED_Z) for
+ * the local z lengths compiled in (32, 48, 64, 80, 96; default
+ * factorisation; an even number of modes per plane; 6 modes per work item;
+ * not for PSATD_HEAT).
+ * 0 -- the generic batched kernels throughout.  PSATD_GENERIC_PLANES turns
+ * both off. */
 int psatd_plane_engine(psatd_plan_t plan, int32_t* engine);
 
 /* Number of kernel launches one psatd_push enqueues for this plan. */

@@ -44,6 +44,10 @@ constexpr int kRegThreads = 128;
 constexpr int kRegX2[] = {32, 40, 48, 56, 64, 72, 88, 96, 104};
 constexpr int kRegY[] = {32, 48, 64, 80, 96};
 constexpr int reg_pitch(int lxh) { return lxh + ((2 - lxh % 4) + 4) % 4; }
+// modes per item of the compiled-length z/Eq. 1 stage (pass B): three pairs,
+// so that the ten fields' pairs fill 30 lanes of a warp; the z lengths it is
+// compiled for are those of kRegY
+constexpr int kRegM = 6;
 
 // Cubic local boxes (side L, ng guards, pass-B chunk M, default splits) that
 // have kernels compiled with their geometry fixed at compile time.
@@ -51,12 +55,25 @@ struct FixedGeo { int L, ng, M; };
 constexpr FixedGeo kFixedF32[5] = {{96, 16, 8}, {64, 16, 8}, {48, 8, 8}, {32, 0, 8}, {96, 16, 4}};
 constexpr FixedGeo kFixedF64[3] = {{96, 16, 4}, {48, 8, 4}, {32, 0, 4}};
 
-// One local FFT axis of length n = f1 * f2, done as two register stages.
-// Forward output (and inverse input) is in "position" order: frequency
-// k1 + f1*k2 sits at position k1*f2 + k2.
+// Three-factor split n = f1 * f2 * f3 (each in 2..16) of a length with no
+// two-factor split: f1 the largest factor in 2..16 whose cofactor has one,
+// (f2, f3) that cofactor's default split; 0 if none exists.
+constexpr int split3_first(int n) {
+    for (int a = kMaxDft; a >= 2; --a)
+        if (n % a == 0 && split_first(n / a) > 0 && n / a > kMaxDft) return a;
+    return 0;
+}
+
+// One local FFT axis of length n = f1 * f2 (f3 <= 1), done as two register
+// stages, or n = f1 * f2 * f3 (f3 > 1), done as three.  Forward output (and
+// inverse input) is in "position" order: frequency k1 + f1*k2 sits at
+// position k1*f2 + k2; with three factors, frequency k1 + f1*k2 + f1*f2*k3
+// sits at position k1*f2*f3 + k2*f3 + k3.
 struct AxisPlan {
     int n, f1, f2;
     int tw;          // offset of the n twiddles exp(-2 pi i m/n) in the pool
+    int f3;          // third factor (0 or 1: a two-factor split)
+    int pad;
 };
 
 // Per subdomain, everything a stage kernel needs (device copy in workspace).

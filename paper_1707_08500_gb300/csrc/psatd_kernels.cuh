@@ -38,7 +38,7 @@
 #define PSATD_MINB_A_FIXED 6    // compile-time geometry: fewer registers live, one more CTA fits
 #endif
 #ifndef PSATD_MINB_B
-#define PSATD_MINB_B 4
+#define PSATD_MINB_B 3    // ten fields of 8 modes x 96 z fill a third of shared memory
 #endif
 #ifndef PSATD_MINB_C
 #define PSATD_MINB_C 5
@@ -50,10 +50,25 @@ namespace psatd {
 template <typename T>
 struct alignas(4 * sizeof(T)) twd { cpx<T> hi, lo; };
 
+// FP32 table twiddles: the hi part alone (PSATD_TW_HILO 0, the default),
+// which the host rounds so that each twiddle's magnitude is as close to 1 as
+// neighbouring FP32 values allow (the transform then stays closer to
+// unitary; the phase error this trades in cancels between a forward
+// transform and its inverse), or hi + lo pairs (PSATD_TW_HILO 1, FP64-exact
+// twiddles at twice the multiply cost).  Measured over 100 FP32 steps
+// against the FP64 oracle: 5.1e-6 (hi alone) and 3.8e-6 (hi + lo).
+#ifndef PSATD_TW_HILO
+#define PSATD_TW_HILO 0
+#endif
+
 template <typename T>
 __device__ __forceinline__ twd<T> ld_tw(const twd<T>* p) {
     twd<T> t;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && !PSATD_TW_HILO) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        t.hi = mk(v.x, v.y);
+        t.lo = mk(0.f, 0.f);
+    } else if constexpr (sizeof(T) == 4) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(p));
         t.hi = mk(v.x, v.y);
         t.lo = mk(v.z, v.w);
@@ -66,11 +81,13 @@ __device__ __forceinline__ twd<T> ld_tw(const twd<T>* p) {
 }
 template <typename T>   // v * w
 __device__ __forceinline__ cpx<T> mul_tw(cpx<T> v, const twd<T>& w) {
-    return cmul_const(v, w.hi.x, w.lo.x, w.hi.y, w.lo.y);
+    if constexpr (sizeof(T) == 4 && !PSATD_TW_HILO) return cmul(v, w.hi);
+    else return cmul_const(v, w.hi.x, w.lo.x, w.hi.y, w.lo.y);
 }
 template <typename T>   // v * conj(w)
 __device__ __forceinline__ cpx<T> mul_tw_conj(cpx<T> v, const twd<T>& w) {
-    return cmul_const(v, w.hi.x, w.lo.x, -w.hi.y, -w.lo.y);
+    if constexpr (sizeof(T) == 4 && !PSATD_TW_HILO) return cmulc(v, w.hi);
+    else return cmul_const(v, w.hi.x, w.lo.x, -w.hi.y, -w.lo.y);
 }
 
 template <typename T>
@@ -97,8 +114,6 @@ struct Args {
 };
 
 
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <typename T> struct vec2;
 template <> struct vec2<float> { using type = float2; };
@@ -239,23 +254,102 @@ __device__ __forceinline__ void stage_block(cpx<T>* sm, const Batch& bt, int nbl
     });
 }
 
-// natural order in -> position order out
+// Three-factor axes (n = f1 f2 f3, m = f2 f3).  Their first and last
+// stages are the two-factor ones (f1-point DFTs at stride m with w_n^{j r};
+// f3-point DFTs on contiguous blocks); the middle stage and the first inverse
+// stage below use a DFT of run-time size R <= 16 (an R^2 sum with the
+// twiddles w_R^e = w_n^{e n/R} read from the axis table), which keeps the
+// code of this rarely used path small.
+template <bool INV, typename T>
+__device__ __forceinline__ void dft_runtime(cpx<T>* v, int R, const twd<T>* __restrict__ tw_n, int nR) {
+    cpx<T> out[kMaxDft];
+    for (int k = 0; k < R; ++k) {
+        cpx<T> acc = v[0];
+        int e = 0;
+        for (int r = 1; r < R; ++r) {
+            e += k;
+            if (e >= R) e -= R;                   // e = r k mod R
+            const twd<T> w = ld_tw(tw_n + e * nR);
+            acc = acc + (INV ? mul_tw_conj(v[r], w) : mul_tw(v[r], w));
+        }
+        out[k] = acc;
+    }
+    for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+// middle stage, inside each block k1 of length m: f2-point DFTs at stride f3
+// (item j2 in [0, f3)); forward, output r is then multiplied by
+// w_m^{j2 r} = w_n^{j2 r f1}; inverse, the output at position k1 m + j2 + f3 r
+// by conj(w_n^{(j2 + f3 r) k1}).
+template <bool INV, bool TWO, typename T>
+__device__ __forceinline__ void stage_mid(cpx<T>* sm, const Batch& bt, const AxisPlan& ax,
+                                          const twd<T>* __restrict__ tw_n) {
+    const int f1 = ax.f1, f2 = ax.f2, f3 = ax.f3, m = f2 * f3;
+    const int es = bt.es * f3;
+    loop2(bt.count, f1 * f3, [&](int i, int b) {
+        const int k1 = i / f3, j2 = i - k1 * f3;
+        cpx<T>* p = sm + boff<TWO>(bt, b) + (k1 * m + j2) * bt.es;
+        cpx<T> v[kMaxDft];
+        for (int r = 0; r < f2; ++r) v[r] = p[r * es];
+        dft_runtime<INV>(v, f2, tw_n, ax.n / f2);
+        for (int r = 0; r < f2; ++r) {
+            const twd<T> w = ld_tw(tw_n + (INV ? (j2 + f3 * r) * k1 : j2 * r * f1));
+            p[r * es] = INV ? mul_tw_conj(v[r], w) : mul_tw(v[r], w);
+        }
+    });
+}
+
+// first inverse stage: f3-point DFTs on contiguous blocks (block index
+// k = k1 f2 + k2), then output r times conj(w_m^{r k2}) = conj(w_n^{r k2 f1}).
 template <bool TWO, typename T>
+__device__ __forceinline__ void stage_block_m(cpx<T>* sm, const Batch& bt, const AxisPlan& ax,
+                                              const twd<T>* __restrict__ tw_n) {
+    const int f1 = ax.f1, f2 = ax.f2, f3 = ax.f3;
+    loop2(bt.count, f1 * f2, [&](int k, int b) {
+        cpx<T>* p = sm + boff<TWO>(bt, b) + k * f3 * bt.es;
+        cpx<T> v[kMaxDft];
+        for (int r = 0; r < f3; ++r) v[r] = p[r * bt.es];
+        dft_runtime<true>(v, f3, tw_n, ax.n / f3);
+        const int k2 = k - (k / f2) * f2;
+        for (int r = 0; r < f3; ++r) p[r * bt.es] = mul_tw_conj(v[r], ld_tw(tw_n + r * k2 * f1));
+    });
+}
+
+// natural order in -> position order out (THREE: three-factor axes possible).
+// The compiled first and last stages are shared by both splits (one inlined
+// copy each): their stride and block count are run-time values.
+template <bool TWO, typename T, bool THREE = true>
 __device__ __forceinline__ void fft_fwd(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const twd<T>* tw) {
     const twd<T>* w = tw + ax.tw;
-    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, false, true, TWO>(sm, bt, ax.f2, w); });
+    const bool three = THREE && ax.f3 > 1;
+    const int m = three ? ax.f2 * ax.f3 : ax.f2;           // stride of the first stage
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, false, true, TWO>(sm, bt, m, w); });
     __syncthreads();
-    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, false, false, TWO>(sm, bt, ax.f1, w); });
+    if (three) {
+        stage_mid<false, TWO>(sm, bt, ax, w);
+        __syncthreads();
+    }
+    const int last = three ? ax.f3 : ax.f2, nblk = three ? ax.f1 * ax.f2 : ax.f1;
+    with_size(last, [&](auto NL) { stage_block<decltype(NL)::value, false, false, TWO>(sm, bt, nblk, w); });
     __syncthreads();
 }
 
 // position order in -> natural order out (unnormalised)
-template <bool TWO, typename T>
+template <bool TWO, typename T, bool THREE = true>
 __device__ __forceinline__ void fft_inv(cpx<T>* sm, const AxisPlan& ax, const Batch& bt, const twd<T>* tw) {
     const twd<T>* w = tw + ax.tw;
-    with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, true, true, TWO>(sm, bt, ax.f1, w); });
-    __syncthreads();
-    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, true, false, TWO>(sm, bt, ax.f2, w); });
+    const bool three = THREE && ax.f3 > 1;
+    if (three) {
+        stage_block_m<TWO>(sm, bt, ax, w);
+        __syncthreads();
+        stage_mid<true, TWO>(sm, bt, ax, w);
+        __syncthreads();
+    } else {
+        with_size(ax.f2, [&](auto N2) { stage_block<decltype(N2)::value, true, true, TWO>(sm, bt, ax.f1, w); });
+        __syncthreads();
+    }
+    const int m = three ? ax.f2 * ax.f3 : ax.f2;
+    with_size(ax.f1, [&](auto N1) { stage_strided<decltype(N1)::value, true, false, TWO>(sm, bt, m, w); });
     __syncthreads();
 }
 
@@ -286,14 +380,34 @@ constexpr int per_sub_slot() {
     return STAGE == 0 || STAGE == 4 ? 0 : STAGE == 1 ? 1 : STAGE == 5 ? 3 : STAGE == 6 ? 4 : 2;
 }
 
+// Position of frequency k on an axis with a three-factor split.
+__device__ __forceinline__ int pos_of3(int k, const AxisPlan& ax) {
+    const int k1 = k % ax.f1, kk = k / ax.f1;
+    const int k2 = kk % ax.f2, k3 = kk / ax.f2;
+    return (k1 * ax.f2 + k2) * ax.f3 + k3;
+}
+// Unordered pair i of positions (k, h-k) of the packed x transform: the
+// two-factor walk of split_pair, or, with three factors, frequency k = i.
+__device__ __forceinline__ int split_pairs_ax(int h, const AxisPlan& ax) {
+    return ax.f3 > 1 ? h / 2 + 1 : split_pairs(h, ax.f2);
+}
+__device__ __forceinline__ void split_pair_ax(int i, int h, const AxisPlan& ax, int& pa, int& pb) {
+    if (ax.f3 > 1) {
+        pa = pos_of3(i, ax);
+        pb = pos_of3(h - i, ax);
+    } else {
+        split_pair(i, h, ax.f2, pa, pb);
+    }
+}
+
 // Real split after the packed forward x transform: rows r < nrows at
 // p0 + r*pitch hold the h-point transform of z[m] = x[2m] + i x[2m+1] in
 // position order; each becomes the half spectrum X[0..h] of its real row,
 // walking the pairs (k, h-k) directly in position order (see split_pair).
 template <typename T>
-__device__ __forceinline__ void real_split_rows(cpx<T>* p0, int nrows, int pitch, int h, int f2x,
+__device__ __forceinline__ void real_split_rows(cpx<T>* p0, int nrows, int pitch, int h, const AxisPlan& ax,
                                                 const twd<T>* __restrict__ wp) {
-    loop2(nrows, split_pairs(h, f2x), [&](int i, int y) {
+    loop2(nrows, split_pairs_ax(h, ax), [&](int i, int y) {
         cpx<T>* p = p0 + y * pitch;
         if (i == 0) {
             const cpx<T> z0 = p[0];
@@ -301,7 +415,7 @@ __device__ __forceinline__ void real_split_rows(cpx<T>* p0, int nrows, int pitch
             p[h] = mk(z0.x - z0.y, T(0));
         } else {
             int pa, pb;
-            split_pair(i, h, f2x, pa, pb);
+            split_pair_ax(i, h, ax, pa, pb);
             const cpx<T> A = p[pa], Bc = conj(p[pb]);
             const cpx<T> e = scale(A + Bc, T(0.5));
             const cpx<T> dd = A - Bc;
@@ -317,16 +431,16 @@ __device__ __forceinline__ void real_split_rows(cpx<T>* p0, int nrows, int pitch
 // half spectrum into the packed h-point form (C2R: only the real parts of
 // X[0] and X[h] are used).
 template <typename T>
-__device__ __forceinline__ void real_merge_rows(cpx<T>* p0, int nrows, int pitch, int h, int f2x,
+__device__ __forceinline__ void real_merge_rows(cpx<T>* p0, int nrows, int pitch, int h, const AxisPlan& ax,
                                                 const twd<T>* __restrict__ wp) {
-    loop2(nrows, split_pairs(h, f2x), [&](int i, int y) {
+    loop2(nrows, split_pairs_ax(h, ax), [&](int i, int y) {
         cpx<T>* p = p0 + y * pitch;
         if (i == 0) {
             const T x0 = p[0].x, xh = p[h].x;
             p[0] = mk(x0 + xh, x0 - xh);
         } else {
             int pa, pb;
-            split_pair(i, h, f2x, pa, pb);
+            split_pair_ax(i, h, ax, pa, pb);
             const cpx<T> A = p[pa], Bc = conj(p[pb]);
             const cpx<T> e = A + Bc;
             const cpx<T> o = mul_tw_conj(A - Bc, ld_tw(wp + pa));
@@ -426,6 +540,7 @@ struct Tickets {
 // below is a constant.
 struct GeoDyn {
     static constexpr bool kFixed = false;
+    static constexpr bool kThree = true;     // axes may have three-factor splits
     int Lx, Ly, Lz, h, lxh, pitch, q, ng, ngz, nvy, nvz, M, lgM, fs;
     AxisPlan ax, ay, az;
     __device__ explicit GeoDyn(const SubDesc& d)
@@ -438,6 +553,7 @@ struct GeoDyn {
 template <int MB>
 struct GeoDynM {
     static constexpr bool kFixed = false;
+    static constexpr bool kThree = false;
     static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB);
     int Lx, Ly, Lz, h, lxh, pitch, q, ng, ngz, nvy, nvz, fs;
     AxisPlan ax, ay, az;
@@ -449,14 +565,15 @@ struct GeoDynM {
 template <int L, int NG, int MB, int CSZ>
 struct GeoFix {
     static constexpr bool kFixed = true;
+    static constexpr bool kThree = false;
     static constexpr int Lx = L, Ly = L, Lz = L, h = L / 2, lxh = L / 2 + 1, pitch = (L / 2 + 1) | 1;
     static constexpr int q = L * (L / 2 + 1), ng = NG, ngz = NG, nvy = L - 2 * NG, nvz = L - 2 * NG;
     static constexpr int M = MB, lgM = (MB & (MB - 1)) ? -1 : ilog2(MB), fs = pad_field_stride(L, MB, CSZ);
     AxisPlan ax, ay, az;
     __device__ explicit GeoFix(const SubDesc& d)
-        : ax{h, split_first(h), h / split_first(h), d.ax.tw},
-          ay{L, split_first(L), L / split_first(L), d.ay.tw},
-          az{L, split_first(L), L / split_first(L), d.az.tw} {}
+        : ax{h, split_first(h), h / split_first(h), d.ax.tw, 0, 0},
+          ay{L, split_first(L), L / split_first(L), d.ay.tw, 0, 0},
+          az{L, split_first(L), L / split_first(L), d.az.tw, 0, 0} {}
 };
 
 // ---- pass A: x (real) and y forward transforms of one plane ---------------
@@ -484,12 +601,12 @@ k_pass_a(Args<T> a) {
         cp_async_wait_all();
         __syncthreads();
         // x: complex FFT of length h over the Ly rows
-        fft_fwd<false>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1, 1}, a.tw);
+        fft_fwd<false, T, G::kThree>(sm, g.ax, Batch{Ly, pitch, 0, 0, 1, 1}, a.tw);
         // split the packed transform into the half spectrum X[0..h]
-        real_split_rows(sm, Ly, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        real_split_rows(sm, Ly, pitch, h, g.ax, a.tw + d.tw_post);
         __syncthreads();
         // y: complex FFT of length Ly over the lxh columns
-        fft_fwd<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
+        fft_fwd<false, T, G::kThree>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
         cpx<T>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * g.q;
         loop2(lxh, Ly, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
         __syncthreads();
@@ -513,6 +630,67 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     return s;
 }
 
+// Eq. 1a/1b on one mode (ky, kx at position q of the plane, z position zp):
+// p points at its E_x spectrum in a pass-B chunk, the other fields at
+// multiples of fs; E and B are replaced by E' and B'; with rho (nf > 9) the
+// Gauss partial sums of the mode are added to g_res and g_rho.
+template <typename T>
+__device__ __forceinline__ void eq1_mode(const Args<T>& a, const SubDesc& d, cpx<T>* p, int fs, int q, int yp, int xp,
+                                         int zp, int lxh, int Ly, int64_t NM, int64_t Q, T Nfull, T& g_res,
+                                         T& g_rho) {
+    const int nf = a.nf;
+    const T* __restrict__ tk = a.tab + d.tab_k;
+    const T* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q;
+    const T C = __ldg(tb), S = __ldg(tb + NM), Sk = __ldg(tb + 2 * NM), omC = __ldg(tb + 3 * NM);
+    const T omCk = __ldg(tb + 4 * NM), Dk = __ldg(tb + 5 * NM), inv = __ldg(tb + 6 * NM);
+    const T kx = __ldg(tk + xp), ky = __ldg(tk + lxh + yp), kz = __ldg(tk + lxh + Ly + zp);
+    const T hx = kx * inv, hy = ky * inv, hz = kz * inv;
+    cpx<T> E0 = p[0], E1 = p[fs], E2 = p[2 * fs];
+    cpx<T> B0 = p[3 * fs], B1 = p[4 * fs], B2 = p[5 * fs];
+    cpx<T> J0 = p[6 * fs], J1 = p[7 * fs], J2 = p[8 * fs];
+    cpx<T> px, py, pz;
+    if (a.staggered) {
+        const cpx<T>* ph = a.tabc + d.tab_ph;
+        px = ldg_c(ph + xp); py = ldg_c(ph + lxh + yp); pz = ldg_c(ph + lxh + Ly + zp);
+        const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
+        E0 = cmul(E0, px); E1 = cmul(E1, py); E2 = cmul(E2, pz);
+        J0 = cmul(J0, px); J1 = cmul(J1, py); J2 = cmul(J2, pz);
+        B0 = cmul(B0, pyz); B1 = cmul(B1, pxz); B2 = cmul(B2, pxy);
+    }
+    // khat x B, khat x E, khat x J, khat.E, khat.J
+    const cpx<T> hB0 = scale(B2, hy) - scale(B1, hz), hB1 = scale(B0, hz) - scale(B2, hx), hB2 = scale(B1, hx) - scale(B0, hy);
+    const cpx<T> hE0 = scale(E2, hy) - scale(E1, hz), hE1 = scale(E0, hz) - scale(E2, hx), hE2 = scale(E1, hx) - scale(E0, hy);
+    const cpx<T> hJ0 = scale(J2, hy) - scale(J1, hz), hJ1 = scale(J0, hz) - scale(J2, hx), hJ2 = scale(J1, hx) - scale(J0, hy);
+    const cpx<T> dE = scale(E0, hx) + scale(E1, hy) + scale(E2, hz);
+    const cpx<T> dJ = scale(J0, hx) + scale(J1, hy) + scale(J2, hz);
+    // Eq. 1a: E' = C E + i S khat x B - S/k J + (1-C) khat (khat.E) + khat (khat.J)(S/k - dt)
+    const cpx<T> lo = scale(dE, omC) + scale(dJ, Dk);
+    cpx<T> F0 = scale(E0, C) + scale(mul_i(hB0), S) - scale(J0, Sk) + scale(lo, hx);
+    cpx<T> F1 = scale(E1, C) + scale(mul_i(hB1), S) - scale(J1, Sk) + scale(lo, hy);
+    cpx<T> F2 = scale(E2, C) + scale(mul_i(hB2), S) - scale(J2, Sk) + scale(lo, hz);
+    // Eq. 1b: B' = C B - i S khat x E + i (1-C)/k khat x J
+    cpx<T> G0 = scale(B0, C) - scale(mul_i(hE0), S) + scale(mul_i(hJ0), omCk);
+    cpx<T> G1 = scale(B1, C) - scale(mul_i(hE1), S) + scale(mul_i(hJ1), omCk);
+    cpx<T> G2 = scale(B2, C) - scale(mul_i(hE2), S) + scale(mul_i(hJ2), omCk);
+    if (nf > 9) {
+        // Gauss residual i[k].E' - rho on the unnormalised spectrum
+        const cpx<T> rho = p[9 * fs];
+        const cpx<T> div = mul_i(scale(F0, kx) + scale(F1, ky) + scale(F2, kz));
+        const T rx = fma_t(div.x, Nfull, -rho.x);
+        const T ry = fma_t(div.y, Nfull, -rho.y);
+        const T wgt = (xp == 0 || xp == lxh - 1) ? T(1) : T(2);
+        g_res += wgt * (rx * rx + ry * ry);
+        g_rho += wgt * (rho.x * rho.x + rho.y * rho.y);
+    }
+    if (a.staggered) {
+        const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
+        F0 = cmulc(F0, px); F1 = cmulc(F1, py); F2 = cmulc(F2, pz);
+        G0 = cmulc(G0, pyz); G1 = cmulc(G1, pxz); G2 = cmulc(G2, pxy);
+    }
+    p[0] = F0; p[fs] = F1; p[2 * fs] = F2;
+    p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
+}
+
 template <typename T, class G>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k_pass_b(Args<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -532,18 +710,31 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         const int nf = a.nf;
         const int fs = g.fs;                           // padded field stride in shared memory
         cpx<T>* spec = a.spec + d.spec_off;
-        for (int f = 0; f < nf; ++f) {
+        const bool pairs = sizeof(T) == 4 && (Q & 1) == 0 && M >= 2 && (M & 1) == 0 && nf * (M >> 1) <= kThreads;
+        const int MP = M >> 1;
+        if (pairs) {
+            // pairs of modes (16-byte aligned: Q, q0 and M are even),
+            // zero-filled past the ragged end of the plane; thread (field f,
+            // phase r, pair m2) copies rows r, r + R, ... of its mode pair, so
+            // that consecutive lanes read consecutive pairs of one row; E and
+            // B form the first commit group, J and rho the second
+            const int ncol = nf * MP, R = kThreads / ncol;
+            const int m2 = int(threadIdx.x) % MP, fr = int(threadIdx.x) / MP;
+            const int f = fr / R, r = fr - f * R, c = f * MP + m2;
+            if (c < ncol && f >= 6) cp_async_commit();
+            if (c < ncol) {
+                const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<T>));
+                const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0 + (nb ? 2 * m2 : 0) + int64_t(r) * Q;
+                cpx<T>* dst = sm + f * fs + 2 * m2 + r * M;
+                const int64_t step = int64_t(R) * Q;
+                for (int z = r; z < Lz; z += R, src += step, dst += R * M) cp_async16(dst, src, nb);
+            }
+            if (!(c < ncol && f >= 6)) cp_async_commit();
+        }
+        for (int f = 0; f < nf && !pairs; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
             cpx<T>* s = sm + f * fs;
-            if (sizeof(T) == 4 && (Q & 1) == 0 && M >= 2 && (M & 1) == 0) {
-                // pairs of modes (16-byte aligned: Q, q0 and M are even),
-                // zero-filled past the ragged end of the plane
-                loop2(M >> 1, Lz, [&](int z, int m2) {
-                    const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<T>));
-                    const cpx<T>* g = src + int64_t(z) * Q + (nb ? 2 * m2 : 0);
-                    cp_async16(s + z * M + 2 * m2, g, nb);
-                });
-            } else {
+            {
                 loop2(M, Lz, [&](int z, int m) {
                     const cpx<T>* g = src + int64_t(z) * Q + (m < mc ? m : 0);
                     if constexpr (sizeof(T) == 4) cp_async8z(s + z * M + m, g, m < mc ? 8 : 0);
@@ -552,17 +743,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
             }
             if (f == 5) cp_async_commit();          // E and B: the first group
         }
-        cp_async_commit();                          // J (and rho): the second group
+        cp_async_commit();                          // J (and rho): the second group (empty with pairs)
         // transform E and B while J and rho are still arriving
         cp_async_wait_one();
         __syncthreads();
-        fft_fwd<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
+        fft_fwd<true, T, G::kThree>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
         cp_async_wait_all();
         __syncthreads();
-        fft_fwd<true>(sm + 6 * fs, g.az, Batch{(nf - 6) * M, 1, lgM, fs, M, M}, a.tw);
+        fft_fwd<true, T, G::kThree>(sm + 6 * fs, g.az, Batch{(nf - 6) * M, 1, lgM, fs, M, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
-        const T* __restrict__ tk = a.tab + d.tab_k;
         const T Nfull = T(double(Lx) * double(Ly) * double(Lz));
         // Gauss partial sums in the stage's precision (FP64 throughput is a
         // small fraction of FP32 on this part); one FMA forms the residual
@@ -571,63 +761,31 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         T g_res = T(0), g_rho = T(0);
         loop2(M, Lz, [&](int zp, int m) {
             if (m >= mc) return;
-            const int q = q0 + m;
-            const int yp = q / lxh, xp = q - yp * lxh;
-            const T* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q;
-            const T C = __ldg(tb), S = __ldg(tb + NM), Sk = __ldg(tb + 2 * NM), omC = __ldg(tb + 3 * NM);
-            const T omCk = __ldg(tb + 4 * NM), Dk = __ldg(tb + 5 * NM), inv = __ldg(tb + 6 * NM);
-            const T kx = __ldg(tk + xp), ky = __ldg(tk + lxh + yp), kz = __ldg(tk + lxh + Ly + zp);
-            const T hx = kx * inv, hy = ky * inv, hz = kz * inv;
-            cpx<T>* p = sm + zp * M + m;
-            cpx<T> E0 = p[0], E1 = p[fs], E2 = p[2 * fs];
-            cpx<T> B0 = p[3 * fs], B1 = p[4 * fs], B2 = p[5 * fs];
-            cpx<T> J0 = p[6 * fs], J1 = p[7 * fs], J2 = p[8 * fs];
-            cpx<T> px, py, pz;
-            if (a.staggered) {
-                const cpx<T>* ph = a.tabc + d.tab_ph;
-                px = ldg_c(ph + xp); py = ldg_c(ph + lxh + yp); pz = ldg_c(ph + lxh + Ly + zp);
-                const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
-                E0 = cmul(E0, px); E1 = cmul(E1, py); E2 = cmul(E2, pz);
-                J0 = cmul(J0, px); J1 = cmul(J1, py); J2 = cmul(J2, pz);
-                B0 = cmul(B0, pyz); B1 = cmul(B1, pxz); B2 = cmul(B2, pxy);
-            }
-            // khat x B, khat x E, khat x J, khat.E, khat.J
-            const cpx<T> hB0 = scale(B2, hy) - scale(B1, hz), hB1 = scale(B0, hz) - scale(B2, hx), hB2 = scale(B1, hx) - scale(B0, hy);
-            const cpx<T> hE0 = scale(E2, hy) - scale(E1, hz), hE1 = scale(E0, hz) - scale(E2, hx), hE2 = scale(E1, hx) - scale(E0, hy);
-            const cpx<T> hJ0 = scale(J2, hy) - scale(J1, hz), hJ1 = scale(J0, hz) - scale(J2, hx), hJ2 = scale(J1, hx) - scale(J0, hy);
-            const cpx<T> dE = scale(E0, hx) + scale(E1, hy) + scale(E2, hz);
-            const cpx<T> dJ = scale(J0, hx) + scale(J1, hy) + scale(J2, hz);
-            // Eq. 1a: E' = C E + i S khat x B - S/k J + (1-C) khat (khat.E) + khat (khat.J)(S/k - dt)
-            const cpx<T> lo = scale(dE, omC) + scale(dJ, Dk);
-            cpx<T> F0 = scale(E0, C) + scale(mul_i(hB0), S) - scale(J0, Sk) + scale(lo, hx);
-            cpx<T> F1 = scale(E1, C) + scale(mul_i(hB1), S) - scale(J1, Sk) + scale(lo, hy);
-            cpx<T> F2 = scale(E2, C) + scale(mul_i(hB2), S) - scale(J2, Sk) + scale(lo, hz);
-            // Eq. 1b: B' = C B - i S khat x E + i (1-C)/k khat x J
-            cpx<T> G0 = scale(B0, C) - scale(mul_i(hE0), S) + scale(mul_i(hJ0), omCk);
-            cpx<T> G1 = scale(B1, C) - scale(mul_i(hE1), S) + scale(mul_i(hJ1), omCk);
-            cpx<T> G2 = scale(B2, C) - scale(mul_i(hE2), S) + scale(mul_i(hJ2), omCk);
-            if (nf > 9) {
-                // Gauss residual i[k].E' - rho on the unnormalised spectrum
-                const cpx<T> rho = p[9 * fs];
-                const cpx<T> div = mul_i(scale(F0, kx) + scale(F1, ky) + scale(F2, kz));
-                const T rx = fma_t(div.x, Nfull, -rho.x);
-                const T ry = fma_t(div.y, Nfull, -rho.y);
-                const T wgt = (xp == 0 || xp == lxh - 1) ? T(1) : T(2);
-                g_res += wgt * (rx * rx + ry * ry);
-                g_rho += wgt * (rho.x * rho.x + rho.y * rho.y);
-            }
-            if (a.staggered) {
-                const cpx<T> pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
-                F0 = cmulc(F0, px); F1 = cmulc(F1, py); F2 = cmulc(F2, pz);
-                G0 = cmulc(G0, pyz); G1 = cmulc(G1, pxz); G2 = cmulc(G2, pxy);
-            }
-            p[0] = F0; p[fs] = F1; p[2 * fs] = F2;
-            p[3 * fs] = G0; p[4 * fs] = G1; p[5 * fs] = G2;
+            const int q = q0 + m, yp = q / lxh;
+            eq1_mode(a, d, sm + zp * M + m, fs, q, yp, q - yp * lxh, zp, lxh, Ly, NM, int64_t(Q), Nfull, g_res, g_rho);
         });
         __syncthreads();
-        fft_inv<true>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
+        fft_inv<true, T, G::kThree>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
         const int ng = g.ngz, nz = g.nvz;
-        for (int f = 0; f < 6; ++f) {
+        if (pairs) {
+            // valid z planes of E and B as 16-byte mode pairs: thread (field
+            // f, phase r, pair m2) stores rows ng + r, ng + r + R, ...
+            const int ncol = 6 * MP, R = kThreads / ncol;
+            const int m2 = int(threadIdx.x) % MP, fr = int(threadIdx.x) / MP;
+            const int f = fr / R, r = fr - f * R, c = f * MP + m2;
+            if (c < ncol && 2 * m2 + 1 < mc) {
+                cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng + r) * Q + q0 + 2 * m2;
+                const cpx<T>* src = sm + f * fs + (ng + r) * M + 2 * m2;
+                const int64_t step = int64_t(R) * Q;
+                for (int z = r; z < nz; z += R, dst += step, src += R * M)
+                    __stcs(reinterpret_cast<float4*>(dst), *reinterpret_cast<const float4*>(src));
+            } else if (c < ncol && 2 * m2 < mc) {     // a ragged plane end inside the pair
+                cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng + r) * Q + q0 + 2 * m2;
+                const cpx<T>* src = sm + f * fs + (ng + r) * M + 2 * m2;
+                for (int z = r; z < nz; z += R, dst += int64_t(R) * Q, src += R * M) stcs_c(dst, *src);
+            }
+        }
+        for (int f = 0; f < 6 && !pairs; ++f) {
             cpx<T>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng) * Q + q0;
             const cpx<T>* s = sm + f * fs + ng * M;
             loop2(M, nz, [&](int zv, int m) {
@@ -742,12 +900,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
         }
         cp_async_wait_all();
         __syncthreads();
-        fft_inv<false>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
+        fft_inv<false, T, G::kThree>(sm, g.ay, Batch{lxh, 1, 0, 0, pitch, 1}, a.tw);
         // merge the half spectrum of the valid rows into the packed form
         cpx<T>* rows = sm + ng * pitch;
-        real_merge_rows(rows, ny, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        real_merge_rows(rows, ny, pitch, h, g.ax, a.tw + d.tw_post);
         __syncthreads();
-        fft_inv<false>(rows, g.ax, Batch{ny, pitch, 0, 0, 1, 1}, a.tw);
+        fft_inv<false, T, G::kThree>(rows, g.ax, Batch{ny, pitch, 0, 0, 1, 1}, a.tw);
         // store the valid cells of this plane to every box that holds them
         T* out = a.eb[f];
         const T* rp = reinterpret_cast<const T*>(sm);
@@ -807,7 +965,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(Args<T> a) {
         cp_async_wait_all();
         __syncthreads();
         fft_fwd<false>(sm, g.ax, Batch{nr, pitch, 0, 0, 1, 1}, a.tw);
-        real_split_rows(sm, nr, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        real_split_rows(sm, nr, pitch, h, g.ax, a.tw + d.tw_post);
         __syncthreads();
         cpx<T>* dst = a.spec + d.spec_off + int64_t(f * g.Lz + z) * g.q + int64_t(y0) * lxh;
         loop2(lxh, nr, [&](int y, int c) { stcs_c(dst + y * lxh + c, sm[y * pitch + c]); });
@@ -884,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(Args<T> a) {
         }
         cp_async_wait_all();
         __syncthreads();
-        real_merge_rows(sm, nr, pitch, h, g.ax.f2, a.tw + d.tw_post);
+        real_merge_rows(sm, nr, pitch, h, g.ax, a.tw + d.tw_post);
         __syncthreads();
         fft_inv<false>(sm, g.ax, Batch{nr, pitch, 0, 0, 1, 1}, a.tw);
         T* out = a.eb[f];

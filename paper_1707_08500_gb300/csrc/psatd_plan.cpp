@@ -109,14 +109,65 @@ double kheat(int i, int L, double du, int p) {
     return s;
 }
 
-bool factor(int n, int& f1, int& f2) {
-    f1 = split_first(n);   // the most balanced split with both factors in 1..16
-    if (!f1) return false;
-    f2 = n / f1;
+// Split of an axis length: two factors in 1..16 (the most balanced pair),
+// else three in 2..16 (f3 > 1); false if neither exists.
+bool factor(int n, AxisPlan& ax) {
+    ax.f3 = 0;
+    ax.pad = 0;
+    ax.f1 = split_first(n);
+    if (ax.f1) {
+        ax.f2 = n / ax.f1;
+        return true;
+    }
+    ax.f1 = split3_first(n);
+    if (!ax.f1) return false;
+    ax.f2 = split_first(n / ax.f1);
+    ax.f3 = n / ax.f1 / ax.f2;
     return true;
 }
 
+// Natural (frequency) index held at position P of an n-point axis split
+// with first factor f1 (the position order of the forward transforms:
+// frequency k1 + f1 k2 at position k1 f2 + k2, or with three factors
+// k1 + f1 k2 + f1 f2 k3 at position (k1 f2 + k2) f3 + k3).
+int axis_nat(int n, int f1, int P) {
+    const int m = n / f1;
+    if (m <= kMaxDft) return P / m + f1 * (P % m);
+    const int f2 = split_first(m), f3 = m / f2;
+    const int k1 = P / m, rem = P % m, k2 = rem / f3, k3 = rem % f3;
+    return k1 + f1 * (k2 + f2 * k3);
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// FP32 pair (x, y) near (a, b) whose squared norm is closest to r2: among
+// the roundings of a and b and their neighbours two units in the last place
+// away, the pair with the smallest |x^2 + y^2 - r2| (ties: the nearer pair).
+// A unit twiddle (r2 = 1) rounded this way keeps each stage of the FP32
+// transform closer to unitary than independent rounding does.  The phase
+// error it trades in cancels between a forward transform and the inverse
+// that conjugates the same twiddle, while a magnitude error would not; the
+// rotation (C, S) of Eq. 1 is rounded to nearest instead, because its phase
+// error accumulates from step to step.
+void unit_round(double a, double b, double r2, float& x, float& y) {
+    float ca[5], cb[5];
+    ca[2] = float(a);
+    cb[2] = float(b);
+    ca[1] = std::nextafter(ca[2], -INFINITY); ca[0] = std::nextafter(ca[1], -INFINITY);
+    ca[3] = std::nextafter(ca[2], INFINITY); ca[4] = std::nextafter(ca[3], INFINITY);
+    cb[1] = std::nextafter(cb[2], -INFINITY); cb[0] = std::nextafter(cb[1], -INFINITY);
+    cb[3] = std::nextafter(cb[2], INFINITY); cb[4] = std::nextafter(cb[3], INFINITY);
+    double best = INFINITY, bestd = INFINITY;
+    x = ca[2];
+    y = cb[2];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            const double u = ca[i], v = cb[j];
+            const double e = std::fabs((u * u + v * v) - r2);
+            const double dd = (u - a) * (u - a) + (v - b) * (v - b);
+            if (e < best || (e == best && dd < bestd)) { best = e; bestd = dd; x = ca[i]; y = cb[j]; }
+        }
+}
 
 }  // namespace
 
@@ -151,6 +202,7 @@ struct psatd_plan_s {
     int smemA = 0, smemB = 0, smemC = 0, smemR = 0, smemK = 0;
     bool split = false;                // split-plane schedule (row and column launches)
     bool reg = false;                  // FP32 plane stages with compile-time-length transforms
+    bool regB = false;                 // FP32 z/Eq. 1 stage with compile-time-length transforms
     int smemAreg = 0, smemCreg = 0;
     // workspace layout (bytes)
     size_t off_desc = 0, off_seg = 0, off_tw = 0, off_tab = 0, off_tabc = 0, off_gauss = 0, off_work = 0, off_spec = 0, ws_need = 0;
@@ -185,8 +237,8 @@ static std::vector<char> twiddle_image(const psatd_plan_s* p) {
     for (auto& kv : p->tw_off)
         for (int m = 0; m < kv.first; ++m) tw[kv.second + m] = unit_root(m, kv.first);
     for (auto& kv : p->post_off) {
-        const int Lx = kv.first / 32, f1 = kv.first % 32, h = Lx / 2, f2 = h / f1;
-        for (int P = 0; P < h; ++P) tw[kv.second + P] = unit_root(P / f2 + f1 * (P % f2), Lx);
+        const int Lx = kv.first / 32, f1 = kv.first % 32, h = Lx / 2;
+        for (int P = 0; P < h; ++P) tw[kv.second + P] = unit_root(axis_nat(h, f1, P), Lx);
     }
     // each twiddle is stored as (hi, lo): in FP32 lo is the rounding of the
     // remainder so that hi + lo carries the FP64 value; in FP64 lo = 0
@@ -198,7 +250,8 @@ static std::vector<char> twiddle_image(const psatd_plan_s* p) {
     } else {
         std::vector<float> t32(tw.size() * 4);
         for (size_t i = 0; i < tw.size(); ++i) {
-            const float hr = float(tw[i].real()), hi = float(tw[i].imag());
+            float hr, hi;
+            unit_round(tw[i].real(), tw[i].imag(), 1.0, hr, hi);
             t32[4 * i] = hr;
             t32[4 * i + 1] = hi;
             t32[4 * i + 2] = float(tw[i].real() - double(hr));
@@ -226,10 +279,9 @@ static void table_images(const psatd_plan_s* p, double c_dt, const double dx[3],
         // forward transforms: frequency k1 + f1 k2 at position k1 f2 + k2)
         std::vector<int> nat[3];
         for (int a = 0; a < 3; ++a) {
-            int f2 = n[a] / f1[a];
             int len = a == 0 ? lxh : n[a];
             nat[a].resize(len);
-            for (int P = 0; P < n[a]; ++P) nat[a][P] = P / f2 + f1[a] * (P % f2);
+            for (int P = 0; P < n[a]; ++P) nat[a][P] = axis_nat(n[a], f1[a], P);
             if (a == 0) nat[0][h] = h;
         }
         std::vector<double> km[3];
@@ -357,7 +409,7 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     int prec = flags & (PSATD_F32 | PSATD_F64);
     if (prec != PSATD_F32 && prec != PSATD_F64) return bad(PSATD_E_ARG, "flags must hold exactly one of PSATD_F32, PSATD_F64");
     if (flags & ~(PSATD_F32 | PSATD_F64 | PSATD_STAGGERED | PSATD_GAUSS_DIAG | PSATD_PLAIN | PSATD_GRID_PER_ITEM | PSATD_2D |
-                  PSATD_SPLIT_PLANES | PSATD_HEAT | PSATD_HEAT_SOURCE | PSATD_GENERIC_PLANES))
+                  PSATD_SPLIT_PLANES | PSATD_HEAT | PSATD_HEAT_SOURCE | PSATD_GENERIC_PLANES | PSATD_PACKED_Z))
         return bad(PSATD_E_ARG, "unknown flag bits");
     p->flags = flags;
     p->f64 = prec == PSATD_F64;
@@ -425,14 +477,18 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         d.ngz = ngz;
         if (d.L[0] % 2 || d.L[0] < 2) return bad(PSATD_E_UNSUPPORTED, "local x length must be even");
         int h = d.L[0] / 2;
-        if (!factor(h, d.ax.f1, d.ax.f2) || !factor(d.L[1], d.ay.f1, d.ay.f2) || !factor(d.L[2], d.az.f1, d.az.f2))
-            return bad(PSATD_E_UNSUPPORTED, "subdomain " + std::to_string(s) + ": local length is not a product of two factors <= 16");
+        if (!factor(h, d.ax) || !factor(d.L[1], d.ay) || !factor(d.L[2], d.az))
+            return bad(PSATD_E_UNSUPPORTED, "subdomain " + std::to_string(s) +
+                                                ": local length is not a product of two or three factors <= 16");
         if (tuning) {
             AxisPlan* ap[3] = {&d.ax, &d.ay, &d.az};
             const int len[3] = {h, d.L[1], d.L[2]};
             for (int a = 0; a < 3; ++a) {
                 const int f = tuning->f1[a];
-                if (f > 0 && len[a] % f == 0 && len[a] / f <= kMaxDft) { ap[a]->f1 = f; ap[a]->f2 = len[a] / f; }
+                if (f > 0 && ap[a]->f3 <= 1 && len[a] % f == 0 && len[a] / f <= kMaxDft) {
+                    ap[a]->f1 = f;
+                    ap[a]->f2 = len[a] / f;
+                }
             }
         }
         d.ax.n = h; d.ay.n = d.L[1]; d.az.n = d.L[2];
@@ -454,14 +510,12 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
         return off;
     };
     for (auto& d : p->desc) {
-        d.ax.tw = add_tw(d.ax.n);
-        d.ay.tw = add_tw(d.ay.n);
-        d.az.tw = add_tw(d.az.n);
+        for (AxisPlan* ap : {&d.ax, &d.ay, &d.az}) ap->tw = add_tw(ap->n);
     }
     // real-split twiddles exp(-2 pi i k/Lx) stored in the position order of the
     // x transform (entry P holds k = P/f2 + f1*(P%f2)), one table per (Lx, f1)
     for (auto& d : p->desc) {
-        const int key = d.L[0] * 32 + d.ax.f1;
+        const int key = d.L[0] * 32 + d.ax.f1;   // (Lx, f1) fixes the split (axis_nat)
         auto it = p->post_off.find(key);
         if (it == p->post_off.end()) {
             p->post_off[key] = int(p->n_tw);
@@ -495,15 +549,28 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     }
     // --- pass-B chunk, shared memory, work items --------------------------------
     const int csz = p->f64 ? 16 : 8;
+    // FP32 z/Eq. 1 stage with compile-time-length z transforms: every local z
+    // length compiled in, the default z factorisation, an even number of
+    // modes per plane, kRegM modes per item
+    if ((flags & PSATD_PACKED_Z) && !p->f64 && !p->heat && !(flags & PSATD_GENERIC_PLANES) &&
+        (!tuning || !tuning->chunk_b || tuning->chunk_b == kRegM)) {
+        bool ok = true;
+        for (const SubDesc& d : p->desc) {
+            bool in = false;
+            for (int v : kRegY) in = in || v == d.L[2];
+            ok = ok && in && d.az.f1 == split_first(d.L[2]) && d.q % 2 == 0;   // 16-byte mode pairs
+        }
+        p->regB = ok;
+    }
     int64_t iA = 0, iB = 0, iC = 0, iA2 = 0, iC1 = 0, spec = 0, maxspec = 0;
     for (int s = 0; s < nsub; ++s) {
         SubDesc& d = p->desc[s];
-        int M = (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
-        if (!(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 512 modes
+        int M = p->regB ? kRegM : (tuning && tuning->chunk_b) ? tuning->chunk_b : (p->f64 ? 4 : 8);
+        if (!p->regB && !(tuning && tuning->chunk_b) && d.L[2] < 16)   // short z pencils (2D): widen up to 512 modes
             while (M < 512 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 48 * 1024) M *= 2;
-        if (!(tuning && tuning->chunk_b) && p->heat)       // one or two fields: wider chunks
+        if (!p->regB && !(tuning && tuning->chunk_b) && p->heat)       // one or two fields: wider chunks
             while (M < 64 && int64_t(p->nf) * d.L[2] * (2 * M) * csz <= 32 * 1024) M *= 2;
-        while (M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
+        while (!p->regB && M > 1 && int64_t(p->nf) * (d.L[2] * M + 16) * csz > 200 * 1024) M /= 2;
         d.chunkB = M;
         d.lgB = 0;
         while ((1 << d.lgB) < M) ++d.lgB;
@@ -579,7 +646,8 @@ int psatd_plan_create_tuned(psatd_plan_t* out, const int32_t global_n[3], const 
     // geometry with that width compiled in
     if (p->variant < 0 && !p->split) {
         bool dflt = true;
-        for (const SubDesc& d : p->desc) dflt = dflt && d.chunkB == (p->f64 ? 4 : 8);
+        for (const SubDesc& d : p->desc)
+            dflt = dflt && d.chunkB == (p->f64 ? 4 : 8) && d.ax.f3 <= 1 && d.ay.f3 <= 1 && d.az.f3 <= 1;
         if (dflt) p->variant = -2;
     }
     if (p->smemB > kPlaneSmemMax || (p->split && std::max(p->smemR, p->smemK) > kPlaneSmemMax))
@@ -720,7 +788,7 @@ int psatd_geometry_variant(psatd_plan_t p, int32_t* v) {
 
 int psatd_plane_engine(psatd_plan_t p, int32_t* engine) {
     if (!p || !engine) return PSATD_E_ARG;
-    *engine = p->reg ? 1 : 0;
+    *engine = (p->reg ? 1 : 0) | (p->regB ? 2 : 0);
     return PSATD_OK;
 }
 
@@ -973,7 +1041,11 @@ static int launch_push(psatd_plan_s* p, LaunchCommon c, double* gauss_dev, cudaS
             if ((e = stage(p, 5, c, r.a20, r.a2n, p->smemK, s)) != cudaSuccess) return cuda_fail(p, e, "y columns launch");
         }
         if (!p->plain && (e = mark(1)) != cudaSuccess) return cuda_fail(p, e, "event record");
-        if ((e = stage(p, p->heat ? 8 : 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        if (p->regB) {
+            if ((e = launch_stage_reg(1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) return cuda_fail(p, e, "pass B launch");
+        } else if ((e = stage(p, p->heat ? 8 : 1, c, r.b0, r.bn, p->smemB, s)) != cudaSuccess) {
+            return cuda_fail(p, e, "pass B launch");
+        }
         if (!p->plain && (e = mark(2)) != cudaSuccess) return cuda_fail(p, e, "event record");
         if (p->reg) {
             if ((e = launch_stage_reg(2, c, r.c0, r.cn, p->smemCreg, s)) != cudaSuccess) return cuda_fail(p, e, "pass C launch");

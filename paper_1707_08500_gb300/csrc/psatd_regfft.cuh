@@ -30,6 +30,9 @@
 #ifndef PSATD_MINB_REG
 #define PSATD_MINB_REG 5
 #endif
+#ifndef PSATD_MINB_REG_B
+#define PSATD_MINB_REG_B 4
+#endif
 
 namespace psatd {
 
@@ -303,18 +306,21 @@ __device__ __forceinline__ void row_inv(cpx<float>* row, const twd<float>* __res
 }
 
 // ---- y: column pairs, four threads per pair ------------------------------------
-// Thread (pair c2, quarter q) works on columns 2 c2 and 2 c2 + 1 (the second
-// may be past the half spectrum: it is then padding, computed on and never
-// stored, or, with `tail` set, neither read nor written); quarter q takes
-// every fourth stage-1 (stride) DFT and every fourth stage-2 (block) DFT.
+// Thread (pair c2, quarter q) works on two columns: 2 c2 and 2 c2 + 1 in
+// passes A and B, c2 and c2 + ceil(lxh/2) in pass C (the second may be past
+// the half spectrum: it is then padding, computed on and never stored, or,
+// with `tail` set, neither read nor written); quarter q takes every fourth
+// stage-1 (stride) DFT and every fourth stage-2 (block) DFT.
 // tw = exp(-2 pi i m/L), m = 0..L-1.
 
-// element pair (columns c, c+1) of row y: one 16-byte access when the pitch
-// is even, two 8-byte accesses otherwise (the second skipped for a tail column)
+// element pair (columns c, c + off2) of row y: one 16-byte access for
+// adjacent columns at an even pitch, two 8-byte accesses otherwise (the second
+// skipped for a tail column)
 struct ColPair {
     cpx<float>* base;   // element (0, c)
     int P;              // row pitch (complex)
     bool v16, tail;
+    int off2;           // the second column: c + off2 (1 with v16)
     __device__ __forceinline__ void ld(int y, cpx<float>& a, cpx<float>& b) const {
         cpx<float>* q = base + y * P;
         if (v16) {
@@ -323,7 +329,7 @@ struct ColPair {
             b = mk(v.z, v.w);
         } else {
             a = q[0];
-            b = tail ? mk(0.f, 0.f) : q[1];
+            b = tail ? mk(0.f, 0.f) : q[off2];
         }
     }
     __device__ __forceinline__ void st(int y, cpx<float> a, cpx<float> b) const {
@@ -332,7 +338,7 @@ struct ColPair {
             sts4(q, a, b);
         } else {
             q[0] = a;
-            if (!tail) q[1] = b;
+            if (!tail) q[off2] = b;
         }
     }
 };
@@ -374,6 +380,21 @@ __device__ __forceinline__ void col_fwd2(const ColPair& cp, int q, cpx<float>* d
             stcs_c(d, a[r]);
             if (second) stcs_c(d + 1, b[r]);
         }
+    }
+}
+// forward, stage 2 kept in shared memory (position order, in place)
+template <int LY>
+__device__ __forceinline__ void col_fwd2s(const ColPair& cp, int q) {
+    constexpr int F1 = split_first(LY), F2 = LY / F1;
+#pragma unroll 1
+    for (int k = q; k < F1; k += 4) {
+        cpx<float> a[F2], b[F2];
+#pragma unroll
+        for (int r = 0; r < F2; ++r) cp.ld(k * F2 + r, a[r], b[r]);
+        Dft<F2, false>::run(a);
+        Dft<F2, false>::run(b);
+#pragma unroll
+        for (int r = 0; r < F2; ++r) cp.st(k * F2 + r, a[r], b[r]);
     }
 }
 // inverse, stage 1: F2-point DFTs on contiguous blocks, twiddle conj(w^{r k})
@@ -464,7 +485,7 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_a_reg(Args
         __syncthreads();
         // y: warp q takes quarter q of the DFTs of column pair (2 c2, 2 c2 + 1)
         const int c2 = threadIdx.x & 31, q = threadIdx.x >> 5;
-        const ColPair cp{sm + 2 * c2, P, true, false};
+        const ColPair cp{sm + 2 * c2, P, true, false, 1};
         const bool act = 2 * c2 < lxh;
         if (act) dispatch_y<0>(Ly, [&](auto lc) { col_fwd1<decltype(lc)::value>(cp, q, a.tw + d.ay.tw); });
         __syncthreads();
@@ -517,9 +538,11 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_c_reg(Args
         }
         if (!wait_bulk(&bar, parity, a.err, &s_ok)) return;
         parity ^= 1u;
-        const int c2 = threadIdx.x & 31, q = threadIdx.x >> 5;
-        const ColPair cp{sm + 2 * c2, P, false, 2 * c2 + 1 >= lxh};
-        const bool act = 2 * c2 < lxh;
+        // columns c2 and c2 + np (np = ceil(lxh/2)): consecutive lanes touch
+        // consecutive 8-byte elements, free of bank conflicts at the odd pitch
+        const int c2 = threadIdx.x & 31, q = threadIdx.x >> 5, np = (lxh + 1) >> 1;
+        const ColPair cp{sm + c2, P, false, c2 + np >= lxh, np};
+        const bool act = c2 < np;
         if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv1<decltype(lc)::value>(cp, q, a.tw + d.ay.tw); });
         __syncthreads();
         if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv2<decltype(lc)::value>(cp, q); });
@@ -547,6 +570,286 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_c_reg(Args
                 });
             } else {
                 loop2n<kRegThreads>(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- packed column pairs (P2 lanes: the two columns) ---------------------------
+// A pair of complex numbers (a, b) as C2: x = (re a, re b), y = (im a, im b).
+// In shared memory a pair is 16 bytes, either interleaved per number
+// ("aos": re a, im a, re b, im b, the layout of the spectra) or by part
+// ("planar": re a, re b, im a, im b, the layout between the packed stages).
+using C2 = cpx<P2>;
+__device__ __forceinline__ C2 ld_aos(const cpx<float>* q) {
+    const float4 v = lds4(q);
+    return mk(P2(v.x, v.z), P2(v.y, v.w));
+}
+__device__ __forceinline__ C2 ld_pl(const cpx<float>* q) {
+    const float4 v = lds4(q);
+    return mk(P2(v.x, v.y), P2(v.z, v.w));
+}
+__device__ __forceinline__ void st_pl(cpx<float>* q, C2 c) {
+    *reinterpret_cast<float4*>(q) = make_float4(c.x.x, c.x.y, c.y.x, c.y.y);
+}
+__device__ __forceinline__ void st_aos(cpx<float>* q, C2 c) {
+    *reinterpret_cast<float4*>(q) = make_float4(c.x.x, c.y.x, c.x.y, c.y.y);
+}
+// v * w and v * conj(w) for one twiddle w shared by both lanes
+__device__ __forceinline__ C2 mul_tw2(C2 v, const twd<float>& w) {
+    const P2 c(w.hi.x), s(w.hi.y), ms(-w.hi.y);
+    return mk(fma_t(v.x, c, v.y * ms), fma_t(v.x, s, v.y * c));
+}
+__device__ __forceinline__ C2 mul_tw2_conj(C2 v, const twd<float>& w) {
+    const P2 c(w.hi.x), s(w.hi.y), ms(-w.hi.y);
+    return mk(fma_t(v.x, c, v.y * s), fma_t(v.y, c, v.x * ms));
+}
+
+// z transforms of a column pair of the pass-B chunk (pair base `col`, row
+// pitch P complex), quarter q of the DFTs as in col_fwd1 / col_fwd2 /
+// col_inv1 / col_inv2.  Forward stage 1 reads the interleaved spectra and
+// writes planar pairs; inverse stage 2 reads planar pairs and writes the
+// interleaved spectra back.
+template <int LZ>
+__device__ __forceinline__ void zp_fwd1(cpx<float>* col, int P, int q, const twd<float>* __restrict__ tw) {
+    constexpr int F1 = split_first(LZ), F2 = LZ / F1;
+#pragma unroll 1
+    for (int j = q; j < F2; j += 4) {
+        C2 v[F1];
+#pragma unroll
+        for (int r = 0; r < F1; ++r) v[r] = ld_aos(col + (j + F2 * r) * P);
+        Dft<F1, false>::run(v);
+        st_pl(col + j * P, v[0]);
+#pragma unroll
+        for (int r = 1; r < F1; ++r) st_pl(col + (j + F2 * r) * P, mul_tw2(v[r], ld_tw(tw + j * r)));
+    }
+}
+template <int LZ>
+__device__ __forceinline__ void zp_fwd2(cpx<float>* col, int P, int q) {
+    constexpr int F1 = split_first(LZ), F2 = LZ / F1;
+#pragma unroll 1
+    for (int k = q; k < F1; k += 4) {
+        C2 v[F2];
+#pragma unroll
+        for (int r = 0; r < F2; ++r) v[r] = ld_pl(col + (k * F2 + r) * P);
+        Dft<F2, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < F2; ++r) st_pl(col + (k * F2 + r) * P, v[r]);
+    }
+}
+template <int LZ>
+__device__ __forceinline__ void zp_inv1(cpx<float>* col, int P, int q, const twd<float>* __restrict__ tw) {
+    constexpr int F1 = split_first(LZ), F2 = LZ / F1;
+#pragma unroll 1
+    for (int k = q; k < F1; k += 4) {
+        C2 v[F2];
+#pragma unroll
+        for (int r = 0; r < F2; ++r) v[r] = ld_pl(col + (k * F2 + r) * P);
+        Dft<F2, true>::run(v);
+        st_pl(col + k * F2 * P, v[0]);
+#pragma unroll
+        for (int r = 1; r < F2; ++r) st_pl(col + (k * F2 + r) * P, mul_tw2_conj(v[r], ld_tw(tw + r * k)));
+    }
+}
+template <int LZ>
+__device__ __forceinline__ void zp_inv2(cpx<float>* col, int P, int q) {
+    constexpr int F1 = split_first(LZ), F2 = LZ / F1;
+#pragma unroll 1
+    for (int j = q; j < F2; j += 4) {
+        C2 v[F1];
+#pragma unroll
+        for (int r = 0; r < F1; ++r) v[r] = ld_pl(col + (j + F2 * r) * P);
+        Dft<F1, true>::run(v);
+#pragma unroll
+        for (int r = 0; r < F1; ++r) st_aos(col + (j + F2 * r) * P, v[r]);
+    }
+}
+
+// Eq. 1a/1b on a pair of modes (positions q, q + 1 of a plane, both at z
+// position zp), packed: p points at the E_x pair in planar layout, the other
+// fields at multiples of fs.  Same arithmetic as eq1_mode, lane by lane.
+__device__ __forceinline__ void eq1_pair(const Args<float>& a, const SubDesc& d, cpx<float>* p, int fs, int q, int yp0,
+                                         int xp0, int yp1, int xp1, int zp, int lxh, int Ly, int64_t NM, int64_t Q,
+                                         P2 Nfull, P2& g_res, P2& g_rho) {
+    const int nf = a.nf;
+    const float* __restrict__ tk = a.tab + d.tab_k;
+    const float* __restrict__ tb = a.tab + d.tab_coef + int64_t(zp) * Q + q;
+    auto ld2 = [&](const float* t) { const float2 v = __ldg(reinterpret_cast<const float2*>(t)); return P2(v.x, v.y); };
+    const P2 C = ld2(tb), S = ld2(tb + NM), Sk = ld2(tb + 2 * NM), omC = ld2(tb + 3 * NM);
+    const P2 omCk = ld2(tb + 4 * NM), Dk = ld2(tb + 5 * NM), inv = ld2(tb + 6 * NM);
+    const P2 kx(__ldg(tk + xp0), __ldg(tk + xp1)), ky(__ldg(tk + lxh + yp0), __ldg(tk + lxh + yp1));
+    const P2 kz(__ldg(tk + lxh + Ly + zp));
+    const P2 hx = kx * inv, hy = ky * inv, hz = kz * inv;
+    const P2 mhx = -hx, mhy = -hy, mhz = -hz, mS = -S, mSk = -Sk, momCk = -omCk;
+    C2 E0 = ld_pl(p), E1 = ld_pl(p + fs), E2 = ld_pl(p + 2 * fs);
+    C2 B0 = ld_pl(p + 3 * fs), B1 = ld_pl(p + 4 * fs), B2 = ld_pl(p + 5 * fs);
+    C2 J0 = ld_pl(p + 6 * fs), J1 = ld_pl(p + 7 * fs), J2 = ld_pl(p + 8 * fs);
+    // complex pair times complex pair, and times its conjugate
+    auto cm = [](C2 u, C2 w) { return mk(fma_t(u.x, w.x, u.y * -w.y), fma_t(u.x, w.y, u.y * w.x)); };
+    auto cmc = [](C2 u, C2 w) { return mk(fma_t(u.x, w.x, u.y * w.y), fma_t(u.y, w.x, u.x * -w.y)); };
+    C2 px, py, pz;
+    if (a.staggered) {
+        const cpx<float>* ph = a.tabc + d.tab_ph;
+        const cpx<float> x0 = ldg_c(ph + xp0), x1 = ldg_c(ph + xp1), y0 = ldg_c(ph + lxh + yp0), y1 = ldg_c(ph + lxh + yp1);
+        const cpx<float> z0 = ldg_c(ph + lxh + Ly + zp);
+        px = mk(P2(x0.x, x1.x), P2(x0.y, x1.y));
+        py = mk(P2(y0.x, y1.x), P2(y0.y, y1.y));
+        pz = mk(P2(z0.x), P2(z0.y));
+        const C2 pyz = cm(py, pz), pxz = cm(px, pz), pxy = cm(px, py);
+        E0 = cm(E0, px); E1 = cm(E1, py); E2 = cm(E2, pz);
+        J0 = cm(J0, px); J1 = cm(J1, py); J2 = cm(J2, pz);
+        B0 = cm(B0, pyz); B1 = cm(B1, pxz); B2 = cm(B2, pxy);
+    }
+    // khat x F (component by component: u * h - w * h')
+    auto cr = [](C2 u, P2 hu, C2 w, P2 mhw) { return mk(fma_t(u.x, hu, w.x * mhw), fma_t(u.y, hu, w.y * mhw)); };
+    const C2 hB0 = cr(B2, hy, B1, mhz), hB1 = cr(B0, hz, B2, mhx), hB2 = cr(B1, hx, B0, mhy);
+    const C2 hE0 = cr(E2, hy, E1, mhz), hE1 = cr(E0, hz, E2, mhx), hE2 = cr(E1, hx, E0, mhy);
+    const C2 hJ0 = cr(J2, hy, J1, mhz), hJ1 = cr(J0, hz, J2, mhx), hJ2 = cr(J1, hx, J0, mhy);
+    auto dot = [&](C2 u0, C2 u1, C2 u2) {
+        return mk(fma_t(u0.x, hx, fma_t(u1.x, hy, u2.x * hz)), fma_t(u0.y, hx, fma_t(u1.y, hy, u2.y * hz)));
+    };
+    const C2 dE = dot(E0, E1, E2), dJ = dot(J0, J1, J2);
+    // (1-C) khat.E + (S/k - dt) khat.J
+    const C2 lo = mk(fma_t(dE.x, omC, dJ.x * Dk), fma_t(dE.y, omC, dJ.y * Dk));
+    // Eq. 1a: E' = C E + i S khat x B - S/k J + khat lo
+    auto eq_e = [&](C2 e, C2 hb, C2 j, P2 h) {
+        return mk(fma_t(C, e.x, fma_t(mS, hb.y, fma_t(mSk, j.x, h * lo.x))),
+                  fma_t(C, e.y, fma_t(S, hb.x, fma_t(mSk, j.y, h * lo.y))));
+    };
+    // Eq. 1b: B' = C B - i S khat x E + i (1-C)/k khat x J
+    auto eq_b = [&](C2 b, C2 he, C2 hj) {
+        return mk(fma_t(C, b.x, fma_t(S, he.y, momCk * hj.y)), fma_t(C, b.y, fma_t(mS, he.x, omCk * hj.x)));
+    };
+    C2 F0 = eq_e(E0, hB0, J0, hx), F1 = eq_e(E1, hB1, J1, hy), F2 = eq_e(E2, hB2, J2, hz);
+    C2 G0 = eq_b(B0, hE0, hJ0), G1 = eq_b(B1, hE1, hJ1), G2 = eq_b(B2, hE2, hJ2);
+    if (nf > 9) {
+        // |i[k].E' N - rho|^2 = (N sy + rho_x)^2 + (rho_y - N sx)^2 with
+        // s = [k].E'; weighted by the half-spectrum multiplicity
+        const C2 rho = ld_pl(p + 9 * fs);
+        const P2 sx = fma_t(kx, F0.x, fma_t(ky, F1.x, kz * F2.x)), sy = fma_t(kx, F0.y, fma_t(ky, F1.y, kz * F2.y));
+        const P2 rx = fma_t(sy, Nfull, rho.x), ry = fma_t(sx, -Nfull, rho.y);
+        const P2 wgt(xp0 == 0 || xp0 == lxh - 1 ? 1.f : 2.f, xp1 == 0 || xp1 == lxh - 1 ? 1.f : 2.f);
+        g_res = fma_t(wgt, fma_t(rx, rx, ry * ry), g_res);
+        g_rho = fma_t(wgt, fma_t(rho.x, rho.x, rho.y * rho.y), g_rho);
+    }
+    if (a.staggered) {
+        const C2 pyz = cm(py, pz), pxz = cm(px, pz), pxy = cm(px, py);
+        F0 = cmc(F0, px); F1 = cmc(F1, py); F2 = cmc(F2, pz);
+        G0 = cmc(G0, pyz); G1 = cmc(G1, pxz); G2 = cmc(G2, pxy);
+    }
+    st_pl(p, F0); st_pl(p + fs, F1); st_pl(p + 2 * fs, F2);
+    st_pl(p + 3 * fs, G0); st_pl(p + 4 * fs, G1); st_pl(p + 5 * fs, G2);
+}
+
+// ---- pass B -------------------------------------------------------------------
+// Work item (subdomain, kRegM consecutive (ky, kx) modes, all z): the z
+// pencils of every field are copied to shared memory ([field][z][mode]);
+// warp q takes every fourth DFT of each z transform of one mode pair (lane:
+// field and mode pair); Eq. 1 per (z, mode pair); the inverse z transforms
+// of E and B the same way; the valid z planes are stored.  The two modes of
+// a pair share every twiddle and every step, so all arithmetic runs on
+// packed FP32 lanes (one instruction for both modes).
+template <int NT>
+__device__ __forceinline__ float block_sum_n(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+    }
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG_B) k_pass_b_reg(Args<float> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<float>* sm = reinterpret_cast<cpx<float>*>(smraw);
+    __shared__ SubDesc d;
+    __shared__ float red[2][kRegThreads / 32];
+    __shared__ int64_t s_ticket[2];
+    Tickets<float> tk(a, s_ticket);
+    constexpr int M = kRegM, MP = kRegM / 2;
+    for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
+        tk.prefetch();
+        decode_item<1>(a, it, &d);
+        const int Lx = d.L[0], Ly = d.L[1], Lz = d.L[2], Q = d.q, lxh = d.lxh;
+        const int q0 = int(it - d.itemB) * M;
+        const int mc = min(M, Q - q0);
+        const int nf = a.nf, fs = d.fsB;
+        cpx<float>* spec = a.spec + d.spec_off;
+        // pairs of modes (16-byte copies: Q, q0 and M are even), zero-filled
+        // past the ragged end of the plane: thread (column c, phase r) copies
+        // rows z = r, r + 4, ... of mode-pair column c = (field, pair)
+        {
+            const int c = threadIdx.x >> 2, r = threadIdx.x & 3;
+            if (c < nf * MP) {
+                const int f = c / MP, m2 = c - f * MP;
+                const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<float>));
+                const cpx<float>* src = spec + int64_t(f) * Lz * Q + q0 + (nb ? 2 * m2 : 0) + int64_t(r) * Q;
+                cpx<float>* dst = sm + f * fs + 2 * m2 + r * M;
+                const int64_t step = 4 * int64_t(Q);
+#pragma unroll 4
+                for (int z = r; z < Lz; z += 4, src += step, dst += 4 * M) cp_async16(dst, src, nb);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int lf = lane / MP, lp = lane - lf * MP;
+        cpx<float>* col = sm + lf * fs + 2 * lp;          // this lane's mode pair of field lf
+        const twd<float>* twz = a.tw + d.az.tw;
+        if (lf < nf) dispatch_y<0>(Lz, [&](auto lc) { zp_fwd1<decltype(lc)::value>(col, M, q, twz); });
+        __syncthreads();
+        if (lf < nf) dispatch_y<0>(Lz, [&](auto lc) { zp_fwd2<decltype(lc)::value>(col, M, q); });
+        __syncthreads();
+        const int64_t NM = int64_t(Lz) * Q;
+        const P2 Nfull(float(double(Lx) * double(Ly) * double(Lz)));
+        P2 g_res(0.f), g_rho(0.f);
+        // (ky, kx) positions of the chunk's modes: one division per item
+        const int yp0 = q0 / lxh, xp0 = q0 - yp0 * lxh;
+        loop2n<kRegThreads>(MP, Lz, [&](int zp, int m2) {
+            const int m = 2 * m2;
+            if (m >= mc) return;           // mc is even: both modes of the pair are present
+            int xa = xp0 + m, ya = yp0;
+            if (xa >= lxh) { xa -= lxh; ++ya; }          // M <= lxh: at most one wrap
+            int xb = xa + 1, yb = ya;
+            if (xb >= lxh) { xb -= lxh; ++yb; }
+            eq1_pair(a, d, sm + zp * M + m, fs, q0 + m, ya, xa, yb, xb, zp, lxh, Ly, NM, int64_t(Q), Nfull, g_res,
+                     g_rho);
+        });
+        __syncthreads();
+        if (lf < 6) dispatch_y<0>(Lz, [&](auto lc) { zp_inv1<decltype(lc)::value>(col, M, q, twz); });
+        __syncthreads();
+        if (lf < 6) dispatch_y<0>(Lz, [&](auto lc) { zp_inv2<decltype(lc)::value>(col, M, q); });
+        __syncthreads();
+        // valid z planes of E and B, mode pairs as 16-byte stores: thread
+        // (column c, phase r) stores rows ngz + r, ngz + r + 4, ...
+        {
+            const int ng = d.ngz, nz = d.nv[2];
+            const int c = threadIdx.x >> 2, r = threadIdx.x & 3;
+            if (c < 6 * MP) {
+                const int f = c / MP, m2 = c - f * MP;
+                if (2 * m2 < mc) {
+                    cpx<float>* dst = spec + int64_t(f) * Lz * Q + int64_t(ng + r) * Q + q0 + 2 * m2;
+                    const cpx<float>* src = sm + f * fs + (ng + r) * M + 2 * m2;
+                    const int64_t step = 4 * int64_t(Q);
+#pragma unroll 4
+                    for (int z = r; z < nz; z += 4, dst += step, src += 4 * M)
+                        __stcs(reinterpret_cast<float4*>(dst), lds4(src));
+                }
+            }
+        }
+        if (nf > 9) {
+            const double s1 = double(block_sum_n<kRegThreads>(g_res.x + g_res.y, red[0]));
+            const double s2 = double(block_sum_n<kRegThreads>(g_rho.x + g_rho.y, red[1]));
+            if (threadIdx.x == 0) {
+                a.gauss_part[2 * it] = s1;
+                a.gauss_part[2 * it + 1] = s2;
             }
         }
         __syncthreads();

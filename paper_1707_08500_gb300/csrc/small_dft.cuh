@@ -21,6 +21,28 @@ struct alignas(2 * sizeof(T)) cpx {
     T x, y;
 };
 
+// Two FP32 lanes advanced by one packed instruction (FFMA2 / FMUL2 of the
+// sm_100 family): the same operation on two independent data sets, e.g. two
+// columns that share every constant and twiddle.  Additions are issued as
+// fused multiply-adds with a unit factor, which round exactly like an
+// addition.
+struct __align__(8) P2 {
+    float x, y;   // lane 0, lane 1
+    P2() = default;
+    __host__ __device__ constexpr P2(float a) : x(a), y(a) {}
+    __host__ __device__ constexpr P2(float a, float b) : x(a), y(b) {}
+};
+__device__ __forceinline__ float2 f2of(P2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ P2 p2of(float2 a) { return P2(a.x, a.y); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ P2 fma_t(P2 a, P2 b, P2 c) { return p2of(__ffma2_rn(f2of(a), f2of(b), f2of(c))); }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return p2of(__fmul2_rn(f2of(a), f2of(b))); }
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return fma_t(a, P2(1.f), b); }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return fma_t(b, P2(-1.f), a); }
+__device__ __forceinline__ P2 operator-(P2 a) { return a * P2(-1.f); }
+__device__ __forceinline__ P2& operator+=(P2& a, P2 b) { a = a + b; return a; }
+
 template <typename T>
 __host__ __device__ __forceinline__ cpx<T> mk(T x, T y) { cpx<T> r; r.x = x; r.y = y; return r; }
 template <typename T>
@@ -86,26 +108,55 @@ __device__ __forceinline__ void static_for(F&& f) { static_for_impl<0, N>(f); }
 
 // FP32 constants are split into hi + lo (lo = the FP32 rounding of the
 // remainder), so that a product with a constant carries no systematic
-// quantisation error; in FP64 the lo part is dropped.
+// quantisation error; in FP64 the lo part is dropped.  PSATD_DFT_HILO 0
+// keeps only the FP32 rounding.
+#ifndef PSATD_DFT_HILO
+#define PSATD_DFT_HILO 1
+#endif
 template <typename T>
 struct Split32 {
-    static constexpr bool kOn = sizeof(T) == 4;
+    static constexpr bool kOn = sizeof(T) == 4 && PSATD_DFT_HILO;
+};
+template <>
+struct Split32<P2> {
+    static constexpr bool kOn = PSATD_DFT_HILO;
 };
 template <typename T>
 constexpr T hi_of(double v) { return T(v); }
 template <typename T>
 constexpr T lo_of(double v) { return T(v - double(T(v))); }
+template <>
+constexpr P2 hi_of<P2>(double v) { return P2(float(v)); }
+template <>
+constexpr P2 lo_of<P2>(double v) { return P2(float(v - double(float(v)))); }
 
-// v * (c + i s) with c, s given as (hi, lo) pairs
 template <typename T>
-__device__ __forceinline__ cpx<T> cmul_const(cpx<T> v, T ch, T cl, T sh, T sl) {
-    if constexpr (Split32<T>::kOn) {
+constexpr bool kPacked = std::is_same<T, P2>::value;
+
+// v * (c + i s) with c, s given as (hi, lo) pairs; msh, msl = -sh, -sl are
+// passed separately so that packed lanes need no negation instruction (the
+// scalar forms leave the multiply-adds to the compiler)
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul_const4(cpx<T> v, T ch, T cl, T sh, T sl, T msh, T msl) {
+    if constexpr (kPacked<T>) {
+        if constexpr (Split32<T>::kOn) {
+            const T tr = fma_t(v.x, cl, v.y * msl);
+            const T ti = fma_t(v.x, sl, v.y * cl);
+            return mk(fma_t(v.x, ch, fma_t(v.y, msh, tr)), fma_t(v.x, sh, fma_t(v.y, ch, ti)));
+        } else {
+            return mk(fma_t(v.x, ch, v.y * msh), fma_t(v.x, sh, v.y * ch));
+        }
+    } else if constexpr (Split32<T>::kOn) {
         const T tr = fmaf(v.x, cl, -v.y * sl);
         const T ti = fmaf(v.x, sl, v.y * cl);
         return mk(fmaf(v.x, ch, fmaf(-v.y, sh, tr)), fmaf(v.x, sh, fmaf(v.y, ch, ti)));
     } else {
         return mk(v.x * ch - v.y * sh, v.x * sh + v.y * ch);
     }
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul_const(cpx<T> v, T ch, T cl, T sh, T sl) {
+    return cmul_const4(v, ch, cl, sh, sl, T(-sh), T(-sl));
 }
 
 // multiply by exp(sgn 2 pi i M / N), sgn = -1 forward, +1 inverse
@@ -123,7 +174,7 @@ __device__ __forceinline__ cpx<T> twiddle(cpx<T> v) {
     } else {
         constexpr double c = cos2pi(m, N);
         constexpr double s = INV ? sin2pi(m, N) : -sin2pi(m, N);
-        return cmul_const(v, hi_of<T>(c), lo_of<T>(c), hi_of<T>(s), lo_of<T>(s));
+        return cmul_const4(v, hi_of<T>(c), lo_of<T>(c), hi_of<T>(s), lo_of<T>(s), hi_of<T>(-s), lo_of<T>(-s));
     }
 }
 
@@ -151,11 +202,18 @@ struct Dft<4, INV> {
     template <typename T>
     __device__ __forceinline__ static void run(cpx<T>* v) {
         cpx<T> a = v[0] + v[2], b = v[0] - v[2], c = v[1] + v[3], d = v[1] - v[3];
-        cpx<T> id = mul_i(d);
         v[0] = a + c;
         v[2] = a - c;
-        if (INV) { v[1] = b + id; v[3] = b - id; }
-        else     { v[1] = b - id; v[3] = b + id; }
+        if constexpr (kPacked<T>) {
+            // b -/+ i d, written out so that no component is negated on its own
+            const cpx<T> bm = mk(b.x + d.y, b.y - d.x), bp = mk(b.x - d.y, b.y + d.x);
+            if (INV) { v[1] = bp; v[3] = bm; }
+            else     { v[1] = bm; v[3] = bp; }
+        } else {
+            cpx<T> id = mul_i(d);
+            if (INV) { v[1] = b + id; v[3] = b - id; }
+            else     { v[1] = b - id; v[3] = b + id; }
+        }
     }
 };
 
@@ -183,12 +241,22 @@ struct DftPrime {
                 constexpr double c = cos2pi((long)j * k, P);
                 constexpr double s = sin2pi((long)j * k, P);
                 constexpr T ch = hi_of<T>(c), sh = hi_of<T>(s);
-                R.x += a[j - 1].x * ch; R.y += a[j - 1].y * ch;
-                Q.x += b[j - 1].x * sh; Q.y += b[j - 1].y * sh;
+                if constexpr (kPacked<T>) {     // packed lanes: explicit multiply-adds
+                    R.x = fma_t(a[j - 1].x, ch, R.x); R.y = fma_t(a[j - 1].y, ch, R.y);
+                    Q.x = fma_t(b[j - 1].x, sh, Q.x); Q.y = fma_t(b[j - 1].y, sh, Q.y);
+                } else {
+                    R.x += a[j - 1].x * ch; R.y += a[j - 1].y * ch;
+                    Q.x += b[j - 1].x * sh; Q.y += b[j - 1].y * sh;
+                }
                 if constexpr (Split32<T>::kOn) {
                     constexpr T cl = lo_of<T>(c), sl = lo_of<T>(s);
-                    Rl.x += a[j - 1].x * cl; Rl.y += a[j - 1].y * cl;
-                    Ql.x += b[j - 1].x * sl; Ql.y += b[j - 1].y * sl;
+                    if constexpr (kPacked<T>) {
+                        Rl.x = fma_t(a[j - 1].x, cl, Rl.x); Rl.y = fma_t(a[j - 1].y, cl, Rl.y);
+                        Ql.x = fma_t(b[j - 1].x, sl, Ql.x); Ql.y = fma_t(b[j - 1].y, sl, Ql.y);
+                    } else {
+                        Rl.x += a[j - 1].x * cl; Rl.y += a[j - 1].y * cl;
+                        Ql.x += b[j - 1].x * sl; Ql.y += b[j - 1].y * sl;
+                    }
                 }
             });
             if constexpr (Split32<T>::kOn) { R = R + Rl; Q = Q + Ql; }

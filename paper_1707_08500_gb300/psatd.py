@@ -29,6 +29,7 @@ PSATD_SPLIT_PLANES = 0x80
 PSATD_HEAT = 0x100
 PSATD_HEAT_SOURCE = 0x200
 PSATD_GENERIC_PLANES = 0x400
+PSATD_PACKED_Z = 0x800
 
 STATUS = {0: "PSATD_OK", -1: "PSATD_E_ARG", -2: "PSATD_E_SHAPE", -3: "PSATD_E_NOMEM",
           -4: "PSATD_E_CUDA", -5: "PSATD_E_UNSUPPORTED", -6: "PSATD_E_STATE", -7: "PSATD_E_TIMEOUT"}

@@ -152,8 +152,9 @@ def test_exchange_segments_cover_every_local_cell_once(P):
 
 
 def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
-    cases = [("mirror1024", P.PSATD_F32, 0), ("broadband256", P.PSATD_F32, 0), ("mirror1024", P.PSATD_F64, 0),
-             ("yee64", P.PSATD_F64 | P.PSATD_STAGGERED, 1), ("plain32", P.PSATD_F64, 2), ("uneven48", P.PSATD_F32, -2)]
+    G = P.PSATD_GENERIC_PLANES      # the FP32 generic kernels (the compiled-length ones take 6 modes per item)
+    cases = [("mirror1024", P.PSATD_F32 | G, 0), ("broadband256", P.PSATD_F32 | G, 0), ("mirror1024", P.PSATD_F64, 0),
+             ("yee64", P.PSATD_F64 | P.PSATD_STAGGERED, 1), ("plain32", P.PSATD_F64, 2), ("uneven48", P.PSATD_F32 | G, -2)]
     for name, flags, want in cases:
         wl = I.workload(name)
         h = P.psatd_plan_create(wl.global_n, wl.subs, flags)
@@ -165,10 +166,10 @@ def test_fixed_geometry_kernels_are_selected_for_cubic_boxes(P):
     # the default chunk width compiled in), a non-default chunk width to the
     # fully descriptor-driven ones
     wl = I.workload("broadband256")
-    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 8, "f1": [4, 0, 0]})
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32 | G, {"chunk_b": 8, "f1": [4, 0, 0]})
     assert P.psatd_geometry_variant(h) == -2
     P.psatd_destroy(h)
-    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32, {"chunk_b": 6, "f1": [4, 0, 0]})
+    h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32 | G, {"chunk_b": 6, "f1": [4, 0, 0]})
     assert P.psatd_geometry_variant(h) == -1
     P.psatd_destroy(h)
 
@@ -212,11 +213,12 @@ def test_split_plane_schedule_is_chosen_for_large_planes(P):
     h = P.psatd_plan_create(wl.global_n, wl.subs, P.PSATD_F32 | P.PSATD_SPLIT_PLANES)
     assert P.psatd_push_launches(h) == 5 and P.psatd_geometry_variant(h) == -1
     P.psatd_destroy(h)
-    # the largest boxes: x half length and y, z lengths up to 16 x 16
-    h = P.psatd_plan_create((512, 256, 256), [I.Sub((0, 0, 0), (512, 256, 256), 0, 0)], P.PSATD_F32)
+    # lengths beyond 16 x 16 take three factors: a 1024-long x axis is
+    # accepted; a length with a prime factor above 16 is not
+    h = P.psatd_plan_create((1024, 256, 256), [I.Sub((0, 0, 0), (1024, 256, 256), 0, 0)], P.PSATD_F32)
     P.psatd_destroy(h)
     with pytest.raises(P.PsatdError) as e:
-        P.psatd_plan_create((1024, 256, 256), [I.Sub((0, 0, 0), (1024, 256, 256), 0, 0)], P.PSATD_F32)
+        P.psatd_plan_create((1024, 34 * 8, 256), [I.Sub((0, 0, 0), (1024, 34 * 8, 256), 0, 0)], P.PSATD_F32)
     assert e.value.code == -5
 
 
@@ -392,15 +394,21 @@ def test_coefficient_tables_match_the_oracle(P, p_order, staggered):
 
 def test_compiled_length_plane_engine_selection(P):
     """FP32 plans whose local x and y lengths are all compiled in take the
-    plane stages with thread-private transforms (engine 1); FP64, odd or
-    uncompiled lengths, non-default factorisations, the split-plane schedule
-    and PSATD_GENERIC_PLANES take the generic ones (engine 0)."""
+    plane stages with thread-private transforms (bit 1); with PSATD_PACKED_Z,
+    those whose z lengths are compiled in take the packed z/Eq. 1 stage
+    (bit 2).  FP64, odd or uncompiled lengths, non-default factorisations and
+    PSATD_GENERIC_PLANES take the generic kernels; the split-plane schedule
+    keeps only the z/Eq. 1 one."""
+    G, Z = P.PSATD_GENERIC_PLANES, P.PSATD_PACKED_Z
     cases = [("mirror1024", P.PSATD_F32, None, 1), ("broadband256", P.PSATD_F32, None, 1),
              ("uneven48", P.PSATD_F32, None, 1), ("broadband2d", P.PSATD_F32 | P.PSATD_2D, None, 1),
-             ("mirror1024", P.PSATD_F64, None, 0), ("broadband256", P.PSATD_F32 | P.PSATD_GENERIC_PLANES, None, 0),
-             ("broadband256", P.PSATD_F32 | P.PSATD_SPLIT_PLANES, None, 0),
-             ("broadband256", P.PSATD_F32, {"chunk_b": 0, "f1": [6, 0, 0]}, 0),
-             ("broadband256", P.PSATD_F32, {"chunk_b": 0, "f1": [0, 0, 6]}, 1)]
+             ("broadband256", P.PSATD_F32 | Z, None, 3), ("uneven48", P.PSATD_F32 | Z, None, 3),
+             ("broadband2d", P.PSATD_F32 | P.PSATD_2D | Z, None, 1),
+             ("mirror1024", P.PSATD_F64 | Z, None, 0), ("broadband256", P.PSATD_F32 | G | Z, None, 0),
+             ("broadband256", P.PSATD_F32 | P.PSATD_SPLIT_PLANES | Z, None, 2),
+             ("broadband256", P.PSATD_F32 | Z, {"chunk_b": 0, "f1": [6, 0, 0]}, 2),
+             ("broadband256", P.PSATD_F32 | Z, {"chunk_b": 0, "f1": [0, 0, 6]}, 1),
+             ("broadband256", P.PSATD_F32 | Z, {"chunk_b": 8, "f1": [0, 0, 0]}, 1)]
     for name, flags, tuning, want in cases:
         wl = I.workload(name)
         h = P.psatd_plan_create(wl.global_n, wl.subs, flags, tuning)
@@ -409,6 +417,24 @@ def test_compiled_length_plane_engine_selection(P):
         finally:
             P.psatd_destroy(h)
     subs = I.tensor_decomposition([12, 20], [14, 13], [18, 17], 4, 8)     # odd local lengths
-    h = P.psatd_plan_create((32, 27, 35), subs, P.PSATD_F32)
+    h = P.psatd_plan_create((32, 27, 35), subs, P.PSATD_F32 | Z)
     assert P.psatd_plane_engine(h) == 0
     P.psatd_destroy(h)
+
+
+def test_three_factor_lengths_are_accepted(P):
+    """Lengths with no two-factor split but a three-factor one (216, 432 along
+    x, a 1024-long x axis, the 1024 x 512 x 512 grid as one global box) are
+    accepted; a length with a prime factor above 16 is still rejected."""
+    ok = [((32, 400, 16), I.tensor_decomposition([32], [200, 200], [16], 8, 8)),
+          ((416, 16, 16), I.tensor_decomposition([416], [16], [16], 8, 8)),
+          ((1024, 8, 8), I.tensor_decomposition([1024], [8], [8], 0, 0)),
+          ((1024, 512, 512), I.tensor_decomposition([1024], [512], [512], 0, 0))]
+    for g, subs in ok:
+        for flags in (P.PSATD_F32, P.PSATD_F64):
+            h = P.psatd_plan_create(g, subs, flags)
+            assert P.psatd_layout(h, 0)[1] == subs[0].local
+            P.psatd_destroy(h)
+    with pytest.raises(P.PsatdError) as e:
+        P.psatd_plan_create((32, 34 * 16, 16), I.tensor_decomposition([32], [34 * 16], [16], 0, 8), P.PSATD_F32)
+    assert e.value.code == -5

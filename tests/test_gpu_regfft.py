@@ -40,18 +40,22 @@ def _uneven(ng, cuts, nz, two_d=False):
     return I.Workload("reg", g, subs, "broadband", 2, "f32", 1707 + 31, c_dt=0.6, two_d=two_d)
 
 
-# local x lengths n + 2 ng and y lengths all in the compiled sets
+# local x lengths n + 2 ng and y lengths all in the compiled sets (engine
+# bit 1); in the "z" cases the local z lengths too, run with PSATD_PACKED_Z
+# (bit 2: the packed z/Eq. 1 stage)
 CASES = {
-    "ng8": lambda: _uneven(8, ((24, 40, 56, 72, 88), (16, 32, 48, 64, 80)), (17, 23)),
-    "ng16": lambda: _uneven(16, ((16, 24, 32, 40, 56, 64, 72), (16, 32, 48, 64)), (20,)),
-    "twod": lambda: _uneven(8, ((40, 24, 88), (80, 16, 32)), None, two_d=True),
+    "ng8": (lambda: _uneven(8, ((24, 40, 56, 72, 88), (16, 32, 48, 64, 80)), (17, 23)), 1),
+    "ng16": (lambda: _uneven(16, ((16, 24, 32, 40, 56, 64, 72), (16, 32, 48, 64)), (20,)), 1),
+    "twod": (lambda: _uneven(8, ((40, 24, 88), (80, 16, 32)), None, two_d=True), 1),
+    "ng8z": (lambda: _uneven(8, ((24, 40), (16, 32)), (16, 32, 48)), 3),
+    "ng16z": (lambda: _uneven(16, ((32, 64), (16, 48)), (16, 32, 48, 64)), 3),
 }
 
 
-def _run(P, wl, glob, steps, generic, plain=False):
-    flags = P.PSATD_GENERIC_PLANES if generic else 0
-    sol = P.Solver(wl, plain=plain, extra_flags=flags)
-    assert P.psatd_plane_engine(sol.plan) == (0 if generic else 1)
+def _run(P, wl, glob, steps, generic, plain=False, engine=1, gauss=False):
+    flags = P.PSATD_GENERIC_PLANES if generic else (P.PSATD_PACKED_Z if engine & 2 else 0)
+    sol = P.Solver(wl, plain=plain, extra_flags=flags, gauss=gauss)
+    assert P.psatd_plane_engine(sol.plan) == (0 if generic else engine)
     sol.load_global(glob, names=I.EB_NAMES, guards=False)
     sol.load_global(glob, names=("Jx", "Jy", "Jz", "rho"), guards=True)
     sol.exchange()
@@ -65,10 +69,11 @@ def _run(P, wl, glob, steps, generic, plain=False):
 @pytest.mark.parametrize("plain", [False, True])
 @pytest.mark.parametrize("name", list(CASES))
 def test_compiled_length_planes_match_oracle_and_generic(P, name, plain):
-    wl = CASES[name]()
+    make, engine = CASES[name]
+    wl = make()
     glob = I.global_fields(wl)
     steps = 2
-    reg = _run(P, wl, glob, steps, generic=False, plain=plain)
+    reg = _run(P, wl, glob, steps, generic=False, plain=plain, engine=engine)
     gen = _run(P, wl, glob, steps, generic=True, plain=plain)
     ref = _np(glob)
     for _ in range(steps):
@@ -87,10 +92,10 @@ def test_compiled_length_planes_match_oracle_and_generic(P, name, plain):
 
 
 def test_compiled_length_planes_are_deterministic(P):
-    wl = CASES["ng8"]()
+    wl = CASES["ng8z"][0]()
     glob = I.global_fields(wl)
-    a = _run(P, wl, glob, 3, generic=False)
-    b = _run(P, wl, glob, 3, generic=False)
+    a = _run(P, wl, glob, 3, generic=False, engine=3)
+    b = _run(P, wl, glob, 3, generic=False, engine=3)
     for n in I.EB_NAMES:
         assert torch.equal(a.arenas[n], b.arenas[n])
 
@@ -112,3 +117,30 @@ def test_compiled_length_planes_heat(P, source):
     ref = H.heat_run(ref, wl, 0.45, 2)["T"]
     err = H.rel_l2(hs.gather_global(names=("T",))["T"].numpy(), ref)
     assert err < 4e-6, err
+
+
+@pytest.mark.parametrize("staggered", [False, True])
+def test_compiled_length_z_stage_gauss_and_stagger(P, staggered):
+    """The packed z/Eq. 1 stage (PSATD_PACKED_Z) with the Gauss diagnostic
+    (ten fields) and with Yee-staggered components (phase shifts inside
+    Eq. 1), against the oracle: fields and per-subdomain Gauss sums."""
+    import dataclasses
+    wl = dataclasses.replace(_uneven(8, ((24, 40), (16, 32)), (16, 32)), staggered=staggered, fields="wavepacket")
+    glob = I.global_fields(wl)
+    sol = _run(P, wl, glob, 0, generic=False, engine=3, gauss=True)
+    sums = []
+    for _ in range(2):
+        sol.push()
+        torch.cuda.synchronize()
+        sums.append(sol.gauss_sums().copy())
+    ref = _np(glob)
+    osum = []
+    for _ in range(2):
+        gs = []
+        ref = O.step(ref, wl, gauss_out=gs)
+        osum.append(np.array(gs))
+    err = O.rel_l2(_np(sol.gather_global()), ref)
+    assert err < 4e-6, err
+    for a, b in zip(sums, osum):
+        np.testing.assert_allclose(a[:, 1], b[:, 1], rtol=1e-3)
+        np.testing.assert_allclose(a[:, 0], b[:, 0], rtol=1e-3)
