@@ -283,8 +283,9 @@ def run_ours(args, rank, world, local_rank):
              else {"A": "k_pass_a", "B": "k_pass_b", "C": "k_pass_c"})
     if engine & 2:
         names["B"] = "k_pass_b_reg"
-    stages = {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
-                   "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"}
+    stages = {st: {"kernel": names[st], "ms": round(stage_ms[st], 3), "alg_bytes": by[st],
+                   "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1),
+                   "frac": round(by[st] / (stage_ms[st] / 1e3) / 1e9 / peak, 4)} for st in "ABC"}
     achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
     fused_bytes = (16 if gauss else 15) * (4 if prec == "f32" else 8) * local
     result = {
@@ -711,7 +712,8 @@ def run_heat(args, rank, world, local_rank):
     by, local = stage_bytes(wl, 2, esz, nout=1)
     peak, peak_kind = _peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    names = {"A": "k_pass_a", "B": "k_pass_b_heat", "C": "k_pass_c"}
+    reg = P.psatd_plane_engine(sol.plan) & 1
+    names = {"A": "k_pass_a_reg" if reg else "k_pass_a", "B": "k_pass_b_heat", "C": "k_pass_c_reg" if reg else "k_pass_c"}
     achieved = by[dom] / (stage_ms[dom] / 1e3) / 1e9
     valid = wl.valid_cells
     result = {
@@ -722,8 +724,9 @@ def run_heat(args, rank, world, local_rank):
                    "local_n": list(wl.subs[0].local), "guards": wl.subs[0].ng, "order": wl.subs[0].p, "d_dt": d_dt,
                    "source": True, "l2": f"inputs ({local * 2 * esz / 1e9:.1f} GB) larger than L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
-        "stages": {st: {"ms": round(stage_ms[st], 3), "alg_bytes": by[st],
-                        "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1)} for st in "ABC"},
+        "stages": {st: {"kernel": names[st], "ms": round(stage_ms[st], 3), "alg_bytes": by[st],
+                        "gbs": round(by[st] / (stage_ms[st] / 1e3) / 1e9, 1),
+                        "frac": round(by[st] / (stage_ms[st] / 1e3) / 1e9 / peak, 4)} for st in "ABC"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind},
         "step_roofline": {"three_pass_bytes_per_step": sum(by.values()),

@@ -162,8 +162,6 @@ __device__ __forceinline__ void cp_async8z(void* dst, const void* src, int src_b
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// wait until at most one committed group of this thread is still in flight
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // one complex value
 template <typename T>
 __device__ __forceinline__ void cp_async_c(cpx<T>* dst, const cpx<T>* src) {
@@ -615,19 +613,29 @@ k_pass_a(Args<T> a) {
 
 // ---- pass B: z transforms and the Eq. 1 update -----------------------------
 // Sum of v over the CTA (a pairwise tree, in T), returned to thread 0.
+// Block sums of two values at once (warp shuffle trees, then thread 0 adds
+// the warps' partials in order); the results are valid in thread 0 only.
+// The caller synchronises the block before red is written again.
 template <typename T>
-__device__ __forceinline__ T block_sum(T v, T* red) {
+__device__ __forceinline__ void block_sum2(T& v0, T& v1, T* red) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    T s = 0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < kThreads / 32; ++i) s += red[i];
+    if (l == 0) {
+        red[w] = v0;
+        red[kThreads / 32 + w] = v1;
     }
     __syncthreads();
-    return s;
+    if (threadIdx.x == 0) {
+        T s0 = 0, s1 = 0;
+        for (int i = 0; i < kThreads / 32; ++i) s0 += red[i];
+        for (int i = 0; i < kThreads / 32; ++i) s1 += red[kThreads / 32 + i];
+        v0 = s0;
+        v1 = s1;
+    }
 }
 
 // Eq. 1a/1b on one mode (ky, kx at position q of the plane, z position zp):
@@ -696,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
     __shared__ SubDesc d;
-    __shared__ T red[2][kThreads / 32];
+    __shared__ T red[2 * (kThreads / 32)];
     __shared__ int64_t s_ticket[2];
     Tickets<T> tk(a, s_ticket);
     for (int64_t it = tk.current(); it >= 0; tk.advance(), it = tk.current()) {
@@ -716,12 +724,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
             // pairs of modes (16-byte aligned: Q, q0 and M are even),
             // zero-filled past the ragged end of the plane; thread (field f,
             // phase r, pair m2) copies rows r, r + R, ... of its mode pair, so
-            // that consecutive lanes read consecutive pairs of one row; E and
-            // B form the first commit group, J and rho the second
+            // that consecutive lanes read consecutive pairs of one row
             const int ncol = nf * MP, R = kThreads / ncol;
             const int m2 = int(threadIdx.x) % MP, fr = int(threadIdx.x) / MP;
             const int f = fr / R, r = fr - f * R, c = f * MP + m2;
-            if (c < ncol && f >= 6) cp_async_commit();
             if (c < ncol) {
                 const int nb = min(max(mc - 2 * m2, 0), 2) * int(sizeof(cpx<T>));
                 const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0 + (nb ? 2 * m2 : 0) + int64_t(r) * Q;
@@ -729,7 +735,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
                 const int64_t step = int64_t(R) * Q;
                 for (int z = r; z < Lz; z += R, src += step, dst += R * M) cp_async16(dst, src, nb);
             }
-            if (!(c < ncol && f >= 6)) cp_async_commit();
         }
         for (int f = 0; f < nf && !pairs; ++f) {
             const cpx<T>* src = spec + int64_t(f) * Lz * Q + q0;
@@ -741,16 +746,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
                     else cp_async16(s + z * M + m, g, m < mc ? 16 : 0);
                 });
             }
-            if (f == 5) cp_async_commit();          // E and B: the first group
         }
-        cp_async_commit();                          // J (and rho): the second group (empty with pairs)
-        // transform E and B while J and rho are still arriving
-        cp_async_wait_one();
-        __syncthreads();
-        fft_fwd<true, T, G::kThree>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
+        cp_async_commit();
+        // all fields in one batch: the stages' items spread over the block
+        // with fewer partly idle rounds than two batches of 6 and nf - 6
+        // (transforming E and B while J and rho were still arriving was
+        // 1-5% slower)
         cp_async_wait_all();
         __syncthreads();
-        fft_fwd<true, T, G::kThree>(sm + 6 * fs, g.az, Batch{(nf - 6) * M, 1, lgM, fs, M, M}, a.tw);
+        fft_fwd<true, T, G::kThree>(sm, g.az, Batch{nf * M, 1, lgM, fs, M, M}, a.tw);
 
         const int64_t NM = int64_t(Lz) * Q;
         const T Nfull = T(double(Lx) * double(Ly) * double(Lz));
@@ -759,11 +763,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
         // with a single rounding; the per-item sums are accumulated in FP64
         // by the reduction kernel
         T g_res = T(0), g_rho = T(0);
-        loop2(M, Lz, [&](int zp, int m) {
-            if (m >= mc) return;
-            const int q = q0 + m, yp = q / lxh;
-            eq1_mode(a, d, sm + zp * M + m, fs, q, yp, q - yp * lxh, zp, lxh, Ly, NM, int64_t(Q), Nfull, g_res, g_rho);
-        });
+        if (lgM >= 0 && M <= kThreads) {
+            // a power-of-two chunk divides the block: each thread keeps one
+            // mode (its plane position is fixed over the z loop)
+            const int m = int(threadIdx.x) & (M - 1);
+            if (m < mc) {
+                const int q = q0 + m, yp = q / lxh, xp = q - yp * lxh;
+                for (int zp = int(threadIdx.x) >> lgM; zp < Lz; zp += kThreads >> lgM)
+                    eq1_mode(a, d, sm + zp * M + m, fs, q, yp, xp, zp, lxh, Ly, NM, int64_t(Q), Nfull, g_res, g_rho);
+            }
+        } else {
+            loop2(M, Lz, [&](int zp, int m) {
+                if (m >= mc) return;
+                const int q = q0 + m, yp = q / lxh;
+                eq1_mode(a, d, sm + zp * M + m, fs, q, yp, q - yp * lxh, zp, lxh, Ly, NM, int64_t(Q), Nfull, g_res,
+                         g_rho);
+            });
+        }
         __syncthreads();
         fft_inv<true, T, G::kThree>(sm, g.az, Batch{6 * M, 1, lgM, fs, M, M}, a.tw);
         const int ng = g.ngz, nz = g.nvz;
@@ -793,11 +809,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_B : 2) k
             });
         }
         if (nf > 9) {
-            const double s1 = double(block_sum(g_res, red[0]));
-            const double s2 = double(block_sum(g_rho, red[1]));
+            block_sum2(g_res, g_rho, red);
             if (threadIdx.x == 0) {
-                a.gauss_part[2 * it] = s1;
-                a.gauss_part[2 * it + 1] = s2;
+                a.gauss_part[2 * it] = double(g_res);
+                a.gauss_part[2 * it + 1] = double(g_rho);
             }
         }
         __syncthreads();
