@@ -413,6 +413,10 @@ def run_ours(args, rank, world, local_rank):
         s1.record(stream)
         torch.cuda.synchronize()
         scatter_ms = s0.elapsed_time(s1)
+        with torch.cuda.stream(ds):           # first touch of the pinned buffers, untimed
+            for n in I.EB_NAMES:
+                fhost[n].copy_(fdev[0][n], non_blocking=True)
+        torch.cuda.synchronize()
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record(ds)
         with torch.cuda.stream(ds):
