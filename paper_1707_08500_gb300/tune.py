@@ -5,10 +5,13 @@ Each candidate is a plan built with psatd_plan_create_tuned on the same field
 arenas; it is timed per stage with psatd_push_profiled (CUDA events on the
 launching stream).  The search is a coordinate descent: the z factor and the
 chunk width only change pass B; the x and y factors change passes A and C.
-The shape it picks is then checked: one push with it and one push with the
-default shapes, from the same fields, must agree to within the FP32 per-step
-tolerance (the default shapes are the ones the parity tests pin); otherwise
-the default is returned.  Results are cached in a JSON file keyed by the
+The default shapes are a candidate in every coordinate, and the shape it
+picks must beat them over the whole step (a split tuned on the most common
+box also changes the factorisation of boxes of other shapes, which can take
+the plan off the compiled-length plane kernels).  The shape is then checked:
+one push with it and one push with the default shapes, from the same
+fields, must agree to within the FP32 per-step tolerance (the default shapes
+are the ones the parity tests pin); otherwise the default is returned.  Results are cached in a JSON file keyed by the
 decomposition signature, precision, flags and GPU name.
 """
 from __future__ import annotations
@@ -133,11 +136,14 @@ def autotune(wl: I.Workload, flags: int, device="cuda", reps: int = 3, use_cache
     b = _Bench(wl, flags, device)
     sd = max(set(s.local for s in wl.subs), key=lambda L: sum(1 for s in wl.subs if s.local == L))
     lens = (sd[0] // 2, sd[1], sd[2])
+    default = {"chunk_b": 0, "f1": [0, 0, 0]}
     best = {"chunk_b": 0, "f1": [0, 0, 0]}
     t0 = b.time(best, reps)
     log = [("default", best, t0)]
-    # pass B: z split and chunk width
-    bestB, bestT = None, None
+    # pass B: z split and chunk width; the default shapes are a candidate
+    # (with mixed box shapes a split tuned on the most common box changes the
+    # others' factorisations too, which can cost more than it gains)
+    bestB, bestT = (dict(default, f1=[0, 0, 0]), t0[1]) if t0 else (None, None)
     for fz in _divisor_splits(lens[2]):
         for M in ((2, 4, 6, 8, 12, 16) if lens[2] >= 16 else (32, 64, 128, 256, 512)):
             cand = {"chunk_b": M, "f1": [0, 0, fz]}
@@ -147,9 +153,10 @@ def autotune(wl: I.Workload, flags: int, device="cuda", reps: int = 3, use_cache
                 bestB, bestT = cand, t[1]
     if bestB:
         best["chunk_b"], best["f1"][2] = bestB["chunk_b"], bestB["f1"][2]
-    # passes A and C: x then y split
+    # passes A and C: x then y split, the current (default) split included
     for ax in (0, 1):
-        bestAC, bestf = None, None
+        tcur = b.time(best, reps)
+        bestAC, bestf = (tcur[0] + tcur[2], best["f1"][ax]) if tcur else (None, None)
         for f in _divisor_splits(lens[ax]):
             cand = {"chunk_b": best["chunk_b"], "f1": list(best["f1"])}
             cand["f1"][ax] = f
@@ -157,13 +164,17 @@ def autotune(wl: I.Workload, flags: int, device="cuda", reps: int = 3, use_cache
             log.append((("x", "y")[ax], cand, t))
             if t and (bestAC is None or t[0] + t[2] < bestAC):
                 bestAC, bestf = t[0] + t[2], f
-        if bestf:
+        if bestf is not None:
             best["f1"][ax] = bestf
     tb = b.time(best, reps)
-    if best != {"chunk_b": 0, "f1": [0, 0, 0]} and not b.agrees_with_default(best):
+    if best != default and t0 and (tb is None or sum(tb) >= sum(t0)):
+        if verbose:
+            print("tuned shape", best, "is not faster than the default shapes; keeping the default")
+        best, tb = dict(default, f1=[0, 0, 0]), t0
+    if best != default and not b.agrees_with_default(best):
         if verbose:
             print("tuned shape", best, "disagrees with the default shapes; keeping the default")
-        best, tb = {"chunk_b": 0, "f1": [0, 0, 0]}, t0
+        best, tb = dict(default, f1=[0, 0, 0]), t0
     if verbose:
         for name, cand, t in log:
             print(name, cand, t)
