@@ -142,6 +142,28 @@ __device__ __forceinline__ void stcs_c(cpx<T>* p, cpx<T> v) {
     __stcs(reinterpret_cast<V*>(p), w);
 }
 
+// Rows [0, ny) of a segment whose row holds a power-of-two number ex4 <= NT
+// of 16-byte pieces (guard images 16 cells wide, valid rows of 64), from
+// shared memory (row stride rs elements) to global memory (row stride dld):
+// each of the NT threads keeps one piece column and steps down the rows by
+// pointer increments, with no division.  Returns false, storing nothing,
+// for other widths.
+template <int NT, typename T>
+__device__ __forceinline__ bool store_rows_pow2(T* dst, int64_t dld, const T* sp, int rs, int ex4, int ny) {
+    if (ex4 <= 0 || (ex4 & (ex4 - 1)) != 0 || ex4 > NT) return false;
+    const int lg = 31 - __clz(ex4), x4 = int(threadIdx.x) & (ex4 - 1);
+    const int y0 = int(threadIdx.x) >> lg, dyy = NT >> lg;
+    const T* s = sp + y0 * rs + 4 * x4;
+    T* o = dst + int64_t(y0) * dld + 4 * x4;
+    const int64_t ostep = int64_t(dyy) * dld;
+    for (int yy = y0; yy < ny; yy += dyy, s += dyy * rs, o += ostep) {
+        const cpx<T> u = *reinterpret_cast<const cpx<T>*>(s);
+        const cpx<T> w = *reinterpret_cast<const cpx<T>*>(s + 2);
+        stcs4(o, cpx4<T>{u.x, u.y, w.x, w.y});
+    }
+    return true;
+}
+
 // ---- asynchronous global -> shared copies (no register staging) ------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -931,14 +953,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? PSATD_MINB_C : 2) k
             if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
             T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
             const T* sp = rp + sg.y0 * rs + sg.x0;
-            if (sg.vec4) {
+            if (!sg.vec4) {
+                loop2(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
+            } else if (!store_rows_pow2<kThreads>(dst, sg.dLx, sp, rs, sg.ex >> 2, sg.ey)) {
                 loop2(sg.ex >> 2, sg.ey, [&](int yy, int x4) {
                     const cpx<T> u = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4);
                     const cpx<T> w = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4 + 2);
                     stcs4(dst + int64_t(yy) * sg.dLx + 4 * x4, cpx4<T>{u.x, u.y, w.x, w.y});
                 });
-            } else {
-                loop2(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
             }
         }
         __syncthreads();
@@ -1071,14 +1093,14 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(Args<T> a) {
             if (y_lo >= y_hi) continue;
             T* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + y_lo + sg.dy) * sg.dLx + sg.x0 + sg.dx;
             const T* sp = rp + (y_lo - ya) * rs + sg.x0;
-            if (sg.vec4) {
+            if (!sg.vec4) {
+                loop2(sg.ex, y_hi - y_lo, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
+            } else if (!store_rows_pow2<kThreads>(dst, sg.dLx, sp, rs, sg.ex >> 2, y_hi - y_lo)) {
                 loop2(sg.ex >> 2, y_hi - y_lo, [&](int yy, int x4) {
                     const cpx<T> u = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4);
                     const cpx<T> w = *reinterpret_cast<const cpx<T>*>(sp + yy * rs + 4 * x4 + 2);
                     stcs4(dst + int64_t(yy) * sg.dLx + 4 * x4, cpx4<T>{u.x, u.y, w.x, w.y});
                 });
-            } else {
-                loop2(sg.ex, y_hi - y_lo, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
             }
         }
         __syncthreads();

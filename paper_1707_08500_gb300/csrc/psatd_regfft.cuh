@@ -562,29 +562,14 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_c_reg(Args
             if (z < sg.z0 || z >= sg.z0 + sg.ez) continue;
             float* dst = out + sg.dst_off + (int64_t(z + sg.dz) * sg.dLy + sg.y0 + sg.dy) * sg.dLx + sg.x0 + sg.dx;
             const float* sp = rp + sg.y0 * rs + sg.x0;
-            const int ex4 = sg.ex >> 2;
-            if (sg.vec4 && ex4 > 0 && (ex4 & (ex4 - 1)) == 0 && ex4 <= kRegThreads) {
-                // a power-of-two number of 16-byte pieces per row (guard
-                // images 16 cells wide, valid rows of 64): each thread keeps
-                // one column and steps down the rows by pointer increments
-                const int lg = 31 - __clz(ex4), x4 = int(threadIdx.x) & (ex4 - 1);
-                const int y0 = int(threadIdx.x) >> lg, dyy = kRegThreads >> lg;
-                const float* s = sp + y0 * rs + 4 * x4;
-                float* o = dst + int64_t(y0) * sg.dLx + 4 * x4;
-                const int64_t ostep = int64_t(dyy) * sg.dLx;
-                for (int yy = y0; yy < sg.ey; yy += dyy, s += dyy * rs, o += ostep) {
-                    const cpx<float> u = *reinterpret_cast<const cpx<float>*>(s);
-                    const cpx<float> w = *reinterpret_cast<const cpx<float>*>(s + 2);
-                    stcs4(o, cpx4<float>{u.x, u.y, w.x, w.y});
-                }
-            } else if (sg.vec4) {
-                loop2n<kRegThreads>(ex4, sg.ey, [&](int yy, int x4) {
+            if (!sg.vec4) {
+                loop2n<kRegThreads>(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
+            } else if (!store_rows_pow2<kRegThreads>(dst, sg.dLx, sp, rs, sg.ex >> 2, sg.ey)) {
+                loop2n<kRegThreads>(sg.ex >> 2, sg.ey, [&](int yy, int x4) {
                     const cpx<float> u = *reinterpret_cast<const cpx<float>*>(sp + yy * rs + 4 * x4);
                     const cpx<float> w = *reinterpret_cast<const cpx<float>*>(sp + yy * rs + 4 * x4 + 2);
                     stcs4(dst + int64_t(yy) * sg.dLx + 4 * x4, cpx4<float>{u.x, u.y, w.x, w.y});
                 });
-            } else {
-                loop2n<kRegThreads>(sg.ex, sg.ey, [&](int yy, int xx) { __stcs(dst + int64_t(yy) * sg.dLx + xx, sp[yy * rs + xx]); });
             }
         }
         __syncthreads();
