@@ -12,9 +12,10 @@
 //                 and the real split (forward), or the real merge and the
 //                 inverse (pass C), entirely on its own row, so the x phase
 //                 needs no barrier;
-//   y (columns):  a thread works on a pair of adjacent half-spectrum
-//                 columns; the four warps take every fourth f1-point and
-//                 every fourth f2-point DFT of the 32 column pairs.
+//   y (columns):  a thread works on a pair of half-spectrum columns; the
+//                 four warps (eight half-warps when there are at most 16
+//                 pairs) take every fourth (eighth) f1-point and f2-point
+//                 DFT of the column pairs.
 //
 // The DFT bodies are unrolled for the axis lengths listed in kRegX2 / kRegY
 // (compiled per length, dispatched per work item); the loops over them run
@@ -305,17 +306,30 @@ __device__ __forceinline__ void row_inv(cpx<float>* row, const twd<float>* __res
     }
 }
 
-// ---- y: column pairs, four threads per pair ------------------------------------
-// Thread (pair c2, quarter q) works on two columns: 2 c2 and 2 c2 + 1 in
+// ---- y: column pairs, four or eight threads per pair ------------------------
+// Thread (pair c2, group q of nq) works on two columns: 2 c2 and 2 c2 + 1 in
 // passes A and B, c2 and c2 + ceil(lxh/2) in pass C (the second may be past
 // the half spectrum: it is then padding, computed on and never stored, or,
-// with `tail` set, neither read nor written); quarter q takes every fourth
-// stage-1 (stride) DFT and every fourth stage-2 (block) DFT.
+// with `tail` set, neither read nor written); group q takes every nq-th
+// stage-1 (stride) DFT and every nq-th stage-2 (block) DFT.
 // tw = exp(-2 pi i m/L), m = 0..L-1.
 
 // element pair (columns c, c + off2) of row y: one 16-byte access for
 // adjacent columns at an even pitch, two 8-byte accesses otherwise (the second
 // skipped for a tail column)
+// Lanes of the y phase: ceil(lxh/2) column pairs, one per lane, in four
+// groups of 32 lanes (the four warps); with at most 16 pairs in eight groups
+// of 16 (half-warps), so that fewer lanes idle on narrow planes.  Group q
+// takes every nq-th f1- and f2-point DFT.
+static_assert(kRegThreads == 128, "the y phase maps four warps or eight half-warps");
+__device__ __forceinline__ int lane_groups(int lxh) { return (lxh + 1) >> 1 <= 16 ? 8 : 4; }
+__device__ __forceinline__ int lane_col(int lxh) {
+    return (lxh + 1) >> 1 <= 16 ? int(threadIdx.x & 15) : int(threadIdx.x & 31);
+}
+__device__ __forceinline__ int lane_group(int lxh) {
+    return (lxh + 1) >> 1 <= 16 ? int(threadIdx.x >> 4) : int(threadIdx.x >> 5);
+}
+
 struct ColPair {
     cpx<float>* base;   // element (0, c)
     int P;              // row pitch (complex)
@@ -345,10 +359,10 @@ struct ColPair {
 
 // forward, stage 1: F1-point DFTs at stride F2, twiddle w^{j r}, in place
 template <int LY>
-__device__ __forceinline__ void col_fwd1(const ColPair& cp, int q, const twd<float>* __restrict__ tw) {
+__device__ __forceinline__ void col_fwd1(const ColPair& cp, int q, int nq, const twd<float>* __restrict__ tw) {
     constexpr int F1 = split_first(LY), F2 = LY / F1;
 #pragma unroll 1
-    for (int j = q; j < F2; j += 4) {
+    for (int j = q; j < F2; j += nq) {
         cpx<float> a[F1], b[F1];
 #pragma unroll
         for (int r = 0; r < F1; ++r) cp.ld(j + F2 * r, a[r], b[r]);
@@ -365,10 +379,10 @@ __device__ __forceinline__ void col_fwd1(const ColPair& cp, int q, const twd<flo
 // forward, stage 2: F2-point DFTs on contiguous blocks, written to global
 // (row stride `ld` complex, columns c and c+1 at dst[0], dst[1]) in position order
 template <int LY>
-__device__ __forceinline__ void col_fwd2(const ColPair& cp, int q, cpx<float>* dst, int ld, bool second) {
+__device__ __forceinline__ void col_fwd2(const ColPair& cp, int q, int nq, cpx<float>* dst, int ld, bool second) {
     constexpr int F1 = split_first(LY), F2 = LY / F1;
 #pragma unroll 1
-    for (int k = q; k < F1; k += 4) {
+    for (int k = q; k < F1; k += nq) {
         cpx<float> a[F2], b[F2];
 #pragma unroll
         for (int r = 0; r < F2; ++r) cp.ld(k * F2 + r, a[r], b[r]);
@@ -382,27 +396,12 @@ __device__ __forceinline__ void col_fwd2(const ColPair& cp, int q, cpx<float>* d
         }
     }
 }
-// forward, stage 2 kept in shared memory (position order, in place)
-template <int LY>
-__device__ __forceinline__ void col_fwd2s(const ColPair& cp, int q) {
-    constexpr int F1 = split_first(LY), F2 = LY / F1;
-#pragma unroll 1
-    for (int k = q; k < F1; k += 4) {
-        cpx<float> a[F2], b[F2];
-#pragma unroll
-        for (int r = 0; r < F2; ++r) cp.ld(k * F2 + r, a[r], b[r]);
-        Dft<F2, false>::run(a);
-        Dft<F2, false>::run(b);
-#pragma unroll
-        for (int r = 0; r < F2; ++r) cp.st(k * F2 + r, a[r], b[r]);
-    }
-}
 // inverse, stage 1: F2-point DFTs on contiguous blocks, twiddle conj(w^{r k})
 template <int LY>
-__device__ __forceinline__ void col_inv1(const ColPair& cp, int q, const twd<float>* __restrict__ tw) {
+__device__ __forceinline__ void col_inv1(const ColPair& cp, int q, int nq, const twd<float>* __restrict__ tw) {
     constexpr int F1 = split_first(LY), F2 = LY / F1;
 #pragma unroll 1
-    for (int k = q; k < F1; k += 4) {
+    for (int k = q; k < F1; k += nq) {
         cpx<float> a[F2], b[F2];
 #pragma unroll
         for (int r = 0; r < F2; ++r) cp.ld(k * F2 + r, a[r], b[r]);
@@ -418,10 +417,10 @@ __device__ __forceinline__ void col_inv1(const ColPair& cp, int q, const twd<flo
 }
 // inverse, stage 2: F1-point DFTs at stride F2 -> natural order, in place
 template <int LY>
-__device__ __forceinline__ void col_inv2(const ColPair& cp, int q) {
+__device__ __forceinline__ void col_inv2(const ColPair& cp, int q, int nq) {
     constexpr int F1 = split_first(LY), F2 = LY / F1;
 #pragma unroll 1
-    for (int j = q; j < F2; j += 4) {
+    for (int j = q; j < F2; j += nq) {
         cpx<float> a[F1], b[F1];
 #pragma unroll
         for (int r = 0; r < F1; ++r) cp.ld(j + F2 * r, a[r], b[r]);
@@ -483,15 +482,15 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_a_reg(Args
             dispatch_x<0>(Lx, [&](auto lc) { row_fwd<decltype(lc)::value / 2>(row, a.tw + d.ax.tw, a.tw + d.tw_post); });
         }
         __syncthreads();
-        // y: warp q takes quarter q of the DFTs of column pair (2 c2, 2 c2 + 1)
-        const int c2 = threadIdx.x & 31, q = threadIdx.x >> 5;
+        // y: lane group q takes every nq-th DFT of column pair (2 c2, 2 c2 + 1)
+        const int c2 = lane_col(lxh), q = lane_group(lxh), nq = lane_groups(lxh);
         const ColPair cp{sm + 2 * c2, P, true, false, 1};
         const bool act = 2 * c2 < lxh;
-        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_fwd1<decltype(lc)::value>(cp, q, a.tw + d.ay.tw); });
+        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_fwd1<decltype(lc)::value>(cp, q, nq, a.tw + d.ay.tw); });
         __syncthreads();
         if (act) {
             cpx<float>* dst = a.spec + d.spec_off + int64_t(f * Lz + z) * d.q + 2 * c2;
-            dispatch_y<0>(Ly, [&](auto lc) { col_fwd2<decltype(lc)::value>(cp, q, dst, lxh, 2 * c2 + 1 < lxh); });
+            dispatch_y<0>(Ly, [&](auto lc) { col_fwd2<decltype(lc)::value>(cp, q, nq, dst, lxh, 2 * c2 + 1 < lxh); });
         }
         __syncthreads();
     }
@@ -540,12 +539,12 @@ __global__ void __launch_bounds__(kRegThreads, PSATD_MINB_REG) k_pass_c_reg(Args
         parity ^= 1u;
         // columns c2 and c2 + np (np = ceil(lxh/2)): consecutive lanes touch
         // consecutive 8-byte elements, free of bank conflicts at the odd pitch
-        const int c2 = threadIdx.x & 31, q = threadIdx.x >> 5, np = (lxh + 1) >> 1;
+        const int c2 = lane_col(lxh), q = lane_group(lxh), nq = lane_groups(lxh), np = (lxh + 1) >> 1;
         const ColPair cp{sm + c2, P, false, c2 + np >= lxh, np};
         const bool act = c2 < np;
-        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv1<decltype(lc)::value>(cp, q, a.tw + d.ay.tw); });
+        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv1<decltype(lc)::value>(cp, q, nq, a.tw + d.ay.tw); });
         __syncthreads();
-        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv2<decltype(lc)::value>(cp, q); });
+        if (act) dispatch_y<0>(Ly, [&](auto lc) { col_inv2<decltype(lc)::value>(cp, q, nq); });
         __syncthreads();
         if (int(threadIdx.x) < ny) {
             cpx<float>* row = sm + (ng + threadIdx.x) * P;
