@@ -100,11 +100,15 @@ def test_push_matches_oracle(P, name, schedule):
     got = _np(sol.gather_global())
     err = O.rel_l2(got, ref)
     assert err < tol, f"{name}: rel L2 {err:.3e}"
-    # guards hold the owners' values after the step (fused or separate exchange)
+    # guards hold the owners' values after the step (fused or separate
+    # exchange): bit for bit the owners' valid cells on the GPU (the gathered
+    # global arrays), and close to the oracle's
     for s in range(len(wl.subs)):
         for n in I.EB_NAMES:
             exp = O.extract_box(ref[n], wl.subs[s].lo, wl.subs[s].local, O.sub_guards(wl.subs[s]))
+            own = O.extract_box(got[n], wl.subs[s].lo, wl.subs[s].local, O.sub_guards(wl.subs[s]))
             box = sol.box(n, s).double().cpu().numpy()
+            assert np.array_equal(box, own.astype(np.float64)), (name, s, n)
             scale = max(np.abs(exp).max(), 1e-30)
             assert np.abs(box - exp).max() / scale < 50 * tol, (name, s, n)
 
